@@ -1,0 +1,102 @@
+"""Pins for the oracle's Galerkin assembly (Sec. II-A, Eq. 4-5).
+
+Each check compares against something the oracle does not compute itself:
+an independent quadrature, the 5-point finite-difference stencil, exact
+integrals and conservation identities.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem
+from workloads import meshes, params
+
+
+def _bary_by_solve(p):
+    """Barycentric gradients by inverting the affine map (independent route)."""
+    T = np.array([[1.0, p[0, 0], p[0, 1]],
+                  [1.0, p[1, 0], p[1, 1]],
+                  [1.0, p[2, 0], p[2, 1]]])
+    C = np.linalg.inv(T)        # column i holds the coefficients of lambda_i
+    return C[1:, :].T           # [3, 2] gradients
+
+
+def test_element_integrals_against_quadrature():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        p = rng.normal(size=(3, 2))
+        tri = np.array([[0, 1, 2]], dtype=np.int32)
+        area, grad = fem.element_geometry(p, tri)
+        # area by the shoelace formula
+        e1, e2 = p[1] - p[0], p[2] - p[0]
+        shoe = 0.5 * abs(e1[0] * e2[1] - e1[1] * e2[0])
+        assert area[0] == pytest.approx(shoe, rel=1e-13)
+        g = _bary_by_solve(p)
+        assert np.allclose(grad[0], g, rtol=1e-11, atol=1e-11 * np.abs(g).max())
+
+        class M1:
+            xy = p
+            n_nodes = 3
+            n_tri = 1
+        M1.tri = tri
+        Mf, Kf = fem.full_matrices(M1, np.array([2.5]), np.array([0.7]))
+        # edge-midpoint rule integrates quadratics exactly on triangles
+        mids = [(0, 1), (1, 2), (2, 0)]
+        q = np.zeros((3, 3))
+        for (a, b) in mids:
+            lam = np.zeros(3)
+            lam[a] = lam[b] = 0.5
+            q += np.outer(lam, lam) * shoe / 3.0
+        assert np.allclose(Mf.toarray(), 2.5 * q, rtol=1e-12, atol=0)
+        kk = 0.7 * shoe * g @ g.T
+        assert np.allclose(Kf.toarray(), kk, rtol=1e-10, atol=1e-12 * np.abs(kk).max())
+
+
+def test_stiffness_is_five_point_stencil_on_uniform_mesh():
+    nx = 8
+    m = meshes.unit_square(nx)
+    n = m.n_nodes
+    _, Kf = fem.full_matrices(m, np.ones(m.n_tri), np.ones(m.n_tri))
+    K = Kf.toarray()
+    n1 = nx + 1
+    for j in range(1, nx):
+        for i in range(1, nx):
+            k = j * n1 + i
+            row = np.zeros(n)
+            row[k] = 4.0
+            for d in (-1, 1, -n1, n1):
+                row[k + d] = -1.0
+            assert np.allclose(K[k], row, atol=1e-13), (i, j)
+
+
+def test_conservation_identities_annulus():
+    m = meshes.annulus("5k")
+    p = params.annulus_samples(1, 0)[0]
+    sig, nu, *_ = fem.split_params(p, m.n_regions, m.n_phases)
+    Mf, Kf = fem.full_matrices(m, sig[m.region], nu[m.region])
+    area, _ = fem.element_geometry(m.xy, m.tri)
+    ones = np.ones(m.n_nodes)
+    # K annihilates constants (row sums zero before Dirichlet elimination)
+    assert np.abs(Kf @ ones).max() <= 1e-9 * np.abs(Kf.diagonal()).max()
+    # total mass = integral of sigma
+    assert ones @ (Mf @ ones) == pytest.approx(np.sum(sig[m.region] * area), rel=1e-12)
+    # load vectors integrate the winding: 1^T F_p = sum coef |T| over the phase
+    F = fem.full_load_vectors(m)
+    for ph in range(3):
+        sel = m.src_phase == ph
+        assert F[ph].sum() == pytest.approx(np.sum(m.src_coef[sel] * area[sel]), rel=1e-12, abs=1e-18)
+    # symmetric positive definite after Dirichlet elimination
+    d = fem.Discretisation(m, p)
+    assert abs(d.K - d.K.T).max() == 0.0 and abs(d.M - d.M.T).max() == 0.0
+    # total area of the annulus polygon approaches pi (R^2 - r^2)
+    assert area.sum() == pytest.approx(np.pi * (0.1 ** 2 - 0.02 ** 2), rel=1e-3)
+
+
+def test_dirichlet_elimination_and_source():
+    m = meshes.unit_square(16)
+    p = params.square_samples(1)[0]
+    d = fem.Discretisation(m, p)
+    assert d.n == 225 and d.M.shape == (225, 225)
+    # source J0 sin(2 pi 50 t) on the 4x4-cell conductor: at t = 1/200 s,
+    # sum r = J0 * conductor area (all conductor nodes are interior nodes)
+    r = d.source(1.0 / 200.0)
+    assert r.sum() == pytest.approx(p[4] * 0.25 ** 2, rel=1e-12)
