@@ -1,0 +1,181 @@
+/*
+ * mqs.h -- C ABI of the GB300 library for batched implicit-Euler time stepping
+ * of the 2D eddy-current (magnetoquasistatic) finite-element model across
+ * Multi-Level Monte Carlo samples and Parareal time slices.
+ *
+ * Method: Hahn & Schoeps, "Multi-Level Monte Carlo sampling with Parallel-in-
+ * Time Integration for Uncertainty Quantification in Electric Machine
+ * Simulation" (arXiv 2507.19246).  Sec. II-A (Eq. 1-7): the semi-discrete
+ * Galerkin system M da/dt + K a = r advanced by implicit Euler,
+ *     (M/dt + K) a_{k+1} = (M/dt) a_k + r(t_{k+1});
+ * Sec. II-B (Eq. 8-9): Monte Carlo and telescoping MLMC estimators;
+ * Sec. II-C (Eq. 12): the Parareal update.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MQS_OK (0) or a negative MQS_E* code.  On error the
+ *    message of mqs_last_error() (thread-local, owned by the library, valid
+ *    until the next call from the same thread) says what failed.  Errors leave
+ *    the context usable unless the code is MQS_ECUDA from a sticky CUDA error.
+ *  - Host arrays passed in are read during the call and stay owned by the
+ *    caller.  Pointers documented as "host or device" may point to host memory
+ *    or to device memory of the context's GPU; the library detects which.
+ *  - Device state (meshes, batches, results) is owned by the context and lives
+ *    until the matching free call or mqs_destroy.
+ *  - Work is enqueued on the context's CUDA stream and runs asynchronously;
+ *    calls that return values to host memory synchronise that stream.
+ *  - All floating-point data are IEEE binary64 unless stated otherwise.
+ */
+#ifndef MQS_H
+#define MQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MQS_OK        0
+#define MQS_EINVAL   -1   /* invalid argument (size, index, handle, order of calls) */
+#define MQS_ENOMEM   -2   /* device or host allocation failed */
+#define MQS_ECUDA    -3   /* CUDA runtime error */
+#define MQS_ENOTCONV -4   /* a linear solve hit its iteration limit (strict mode only) */
+
+/* arithmetic of the linear solves */
+#define MQS_FP64   0      /* FP64 Jacobi-PCG */
+#define MQS_MIXED  1      /* FP32 matrix values and SpMV inside FP64 PCG, FP64 residual replacement */
+
+/* quantity of interest */
+#define MQS_QOI_ENERGY 0  /* (1/N) sum_{k=1..N} 1/2 a_k^T K a_k (time-averaged magnetic energy) */
+#define MQS_QOI_JOULE  1  /* (1/T) sum_k (a_{k+1}-a_k)^T M (a_{k+1}-a_k) / dt  (Eq. 26, mean joule loss) */
+
+/* per-sample status bits returned by mqs_read_qoi */
+#define MQS_ST_NOTCONV 1  /* some step's linear solve stopped at the iteration limit */
+#define MQS_ST_NONFINITE 2 /* a residual norm became NaN or Inf */
+
+typedef struct mqs_ctx mqs_ctx;
+
+/* Last error message of the calling thread ("" if none). */
+const char* mqs_last_error(void);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (e.g. a PyTorch stream handle) or NULL for the legacy default stream; the
+ * stream is not owned.  *out receives the handle. */
+int mqs_create(mqs_ctx** out, int device, void* cuda_stream);
+
+/* Change the stream later calls enqueue on (not owned; NULL = default). */
+int mqs_set_stream(mqs_ctx* ctx, void* cuda_stream);
+
+/* Free all device state of the context and the context itself. */
+int mqs_destroy(mqs_ctx* ctx);
+
+/* Upload a P1 triangle mesh and build its shared sparsity pattern and the
+ * per-region reference matrices (Sec. II-A, Eq. 4-5): for every material
+ * region r, M_r = int_{region r} N_i N_j and K_r = int_{region r} grad N_i .
+ * grad N_j, and for every source phase p the load vector F_p = sum over the
+ * phase's triangles of coef_T int_T N_i.  Dirichlet nodes (A_z = 0) are
+ * eliminated; the unknowns are the remaining ("free") nodes in increasing
+ * node id.
+ *   n_nodes, xy        host, [n_nodes][2] node coordinates (m)
+ *   n_tri, tri         host, [n_tri][3] node ids (0-based)
+ *   region             host, [n_tri] material region in [0, n_regions)
+ *   n_regions          1..16
+ *   dirichlet          host, [n_nodes] 1 = homogeneous Dirichlet node
+ *   src_phase          host, [n_tri] source phase in [0, n_phases) or -1
+ *   src_coef           host, [n_tri] winding sign / fill factor of the source
+ *   n_phases           0..4
+ *   mesh_id            out: handle
+ * Errors: MQS_EINVAL for out-of-range ids, degenerate triangles, no free node,
+ * or a free node with more than 32 neighbours. */
+int mqs_upload_mesh(mqs_ctx* ctx, int32_t n_nodes, const double* xy,
+                    int32_t n_tri, const int32_t* tri, const int32_t* region,
+                    int32_t n_regions, const uint8_t* dirichlet,
+                    const int32_t* src_phase, const double* src_coef,
+                    int32_t n_phases, int32_t* mesh_id);
+
+/* Free unknowns and nonzeros of the pattern of a mesh. */
+int mqs_mesh_info(mqs_ctx* ctx, int32_t mesh_id, int32_t* n_free, int64_t* nnz);
+
+/* Upload a batch of sample parameters xi (Sec. II-B).  Layout per sample:
+ *   [sigma_0..sigma_{R-1}, nu_0..nu_{R-1}, J0, amp_0..amp_{P-1}, phase_0..phase_{P-1}]
+ * (n_params = 2R + 1 + 2P), conductivity sigma_r (S/m) and reluctivity
+ * nu_r = 1/mu_r (m/H) per region, current density scale J0 (A/m^2) and per
+ * phase amplitude and phase shift (rad).  Phase p carries
+ *   J_p(t) = J0 amp_p sin(2 pi f t - 2 pi p / P + phase_p).
+ *   params      host or device, [n_samples][n_params], n_samples >= 1
+ *   batch_id    out: handle */
+int mqs_set_samples(mqs_ctx* ctx, int32_t mesh_id, int32_t n_samples, int32_t n_params,
+                    const double* params, int32_t* batch_id);
+
+/* Time window [t0, t_end] (s), supply frequency f (Hz) and QoI kind
+ * (MQS_QOI_*) of a batch.  Must be called before mqs_propagate. */
+int mqs_set_time(mqs_ctx* ctx, int32_t batch_id, double t0, double t_end,
+                 double freq_hz, int32_t qoi_kind);
+
+/* Run one MLMC level for every sample of the batch (Eq. 7, Eq. 9, Eq. 12):
+ * the level-l solve with step dt_level and, if dt_prev > 0, the companion
+ * level-(l-1) solve with step dt_prev on the same sample (Q_{l-1} of Eq. 9).
+ * Both start from a(t0) = 0.  Step counts are (t_end - t0)/dt and must be
+ * integers (relative tolerance 1e-9).
+ *   level          MLMC level of the batch (recorded for mqs_mlmc_accumulate)
+ *   n_slices       1: sequential time stepping; M > 1: the level-l solve runs
+ *                  Parareal (Eq. 12) on M slices, coarse step coarse_factor *
+ *                  dt_level; the step count must be a multiple of
+ *                  M * coarse_factor
+ *   max_par_iters  Parareal iteration limit (<= M)
+ *   par_tol        Parareal stop: max_n ||U_n^k - U_n^{k-1}||_2 / max_n ||U_n^k||_2 <= par_tol
+ *   precision      MQS_FP64 or MQS_MIXED
+ *   cg_tol         per-step PCG stop: ||b - A a||_2 <= cg_tol ||b||_2
+ *   cg_max_iters   per-step PCG iteration limit (>= 1)
+ *   par_iters_out  out (may be NULL): Parareal iterations taken (max over samples), 0 if sequential
+ * A sample whose solve hits cg_max_iters gets status MQS_ST_NOTCONV; the call
+ * still returns MQS_OK.  The call synchronises the stream only when Parareal
+ * runs (to test the stopping rule once per iteration). */
+int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level,
+                  double dt_prev, int32_t n_slices, int32_t coarse_factor,
+                  int32_t max_par_iters, double par_tol, int32_t precision,
+                  double cg_tol, int32_t cg_max_iters, int32_t* par_iters_out);
+
+/* Quantities of interest of the last propagate: qoi[s][0] = Q_l, qoi[s][1] =
+ * Q_{l-1} (0 when dt_prev was 0), status[s] = MQS_ST_* bits.
+ *   qoi      host or device, [n_samples][2]
+ *   status   host or device, [n_samples] (may be NULL)
+ * Synchronises the stream when a destination is host memory. */
+int mqs_read_qoi(mqs_ctx* ctx, int32_t batch_id, double* qoi, int32_t* status);
+
+/* Final state a(t_end) of the last propagate: which = 0 the level-l solve,
+ * 1 the level-(l-1) solve.  a: host or device, [n_samples][n_free], free
+ * unknowns in increasing node id. */
+int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a);
+
+/* Solver counters of the last propagate: stats[0] = total PCG iterations of
+ * all lanes, stats[1] = implicit-Euler solve-steps executed (Parareal counts
+ * every executed fine and coarse step), stats[2] = serial-equivalent
+ * solve-steps, stats[3] = DoF count n_free.  Host array of 4. */
+int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats);
+
+/* Apply a sample's matrix: y[s] = X_s x[s] with X = M (which = 0), K (1) or
+ * A = M/dt + K (2) for every sample s of the batch; x, y host or device,
+ * [n_samples][n_free]. */
+int mqs_apply(mqs_ctx* ctx, int32_t batch_id, int32_t which, double dt,
+              const double* x, double* y);
+
+/* MLMC estimator state (Eq. 9).  mqs_mlmc_reset clears n_levels level
+ * records; mqs_mlmc_accumulate adds the batch's Y = Q_l - Q_{l-1} (Q_0 alone
+ * on level 0) to the record of `level` (compensated two-pass mean and
+ * sum of squared deviations per batch, merged across batches by the pairwise
+ * update of Chan, Golub & LeVeque); mqs_mlmc_readout returns per level
+ * [N_l, mean_l, var_l (unbiased)] in levels[n_levels][3] (host), the estimate
+ * sum_l mean_l and the statistical RMSE sqrt(sum_l var_l / N_l). */
+int mqs_mlmc_reset(mqs_ctx* ctx, int32_t n_levels);
+int mqs_mlmc_accumulate(mqs_ctx* ctx, int32_t batch_id, int32_t level);
+int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rmse);
+
+/* Release a batch or a mesh (a mesh must have no live batch). */
+int mqs_free_batch(mqs_ctx* ctx, int32_t batch_id);
+int mqs_free_mesh(mqs_ctx* ctx, int32_t mesh_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MQS_H */

@@ -1,0 +1,1000 @@
+// C ABI of the library (declared in include/mqs.h): context and handle
+// management, the mesh pattern build, batch set-up, the propagate driver for
+// sequential and Parareal time stepping, readouts and the MLMC estimator.
+#include "mqs_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+namespace mqs {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+namespace {
+
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr int kReplaceEvery = 50;
+
+enum { V_A0, V_A1, V_Y, V_R, V_P, V_Q, V_Z, V_B, kNV64 };
+enum { W_P32, W_Q32, kNV32 };
+
+struct ValueSet {
+  double dt = 0.0;
+  DevBuf A, A32, Dinv;
+};
+
+struct LaneSet {
+  int lanes = 0;
+  int64_t xs = 0;
+  int n = 0;
+  DevBuf v64, v32, amp, phi, k0, qraw, status, iters, tiles;
+  std::vector<TileDesc> host_tiles;
+  int ensure(int lanes_, int64_t xs_, int n_, bool mixed) {
+    lanes = lanes_;
+    xs = xs_;
+    n = n_;
+    const size_t per = (size_t)n * (size_t)xs;
+    MQS_TRY(v64.ensure(per * kNV64 * sizeof(double)));
+    if (mixed) MQS_TRY(v32.ensure(per * kNV32 * sizeof(float)));
+    MQS_TRY(amp.ensure((size_t)xs * kMaxPhases * sizeof(double)));
+    MQS_TRY(phi.ensure((size_t)xs * kMaxPhases * sizeof(double)));
+    MQS_TRY(k0.ensure((size_t)xs * sizeof(int32_t)));
+    MQS_TRY(qraw.ensure((size_t)xs * sizeof(double)));
+    MQS_TRY(status.ensure((size_t)xs * sizeof(int32_t)));
+    MQS_TRY(iters.ensure((size_t)xs * sizeof(double)));
+    return MQS_OK;
+  }
+  double* vec(int j) const { return v64.as<double>() + (size_t)j * n * xs; }
+  float* vec32(int j) const { return v32.p ? v32.as<float>() + (size_t)j * n * xs : nullptr; }
+  LaneArrays arrays() const {
+    return LaneArrays{amp.as<double>(), phi.as<double>(), k0.as<int32_t>(), qraw.as<double>(),
+                      status.as<int32_t>(), iters.as<double>()};
+  }
+};
+
+struct Batch {
+  int mesh_id = -1;
+  int n = 0, n_params = 0;
+  DevBuf params;
+  bool time_set = false;
+  double t0 = 0.0, t_end = 0.0, freq = 50.0;
+  int qoi_kind = MQS_QOI_JOULE;
+  DevBuf Mv, Kv;
+  bool have_M = false, have_K = false;
+  std::vector<std::unique_ptr<ValueSet>> vsets;
+  LaneSet plain, par, chain;
+  int nf_pad = 0, nc_pad = 0;
+  bool has_coarse = false;
+  DevBuf U, G, jump2, norm2;
+  int mode = 0;      // 0 nothing run, 1 sequential, 2 Parareal
+  int M = 0;
+  DevBuf qoi, status;
+  int level = 0;
+  double stats[4] = {0, 0, 0, 0};
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_sm = 1;
+  std::vector<std::unique_ptr<MeshDev>> meshes;
+  std::vector<std::unique_ptr<Batch>> batches;
+  DevBuf mlmc;
+  int n_levels = 0;
+};
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace mqs
+
+struct mqs_ctx {
+  mqs::Ctx c;
+};
+
+using namespace mqs;
+
+namespace {
+
+int enter(mqs_ctx* ctx) {
+  clear_error();
+  if (!ctx) {
+    set_error("null context");
+    return MQS_EINVAL;
+  }
+  MQS_CUDA_TRY(cudaSetDevice(ctx->c.device));
+  return MQS_OK;
+}
+
+MeshDev* get_mesh(mqs_ctx* ctx, int id) {
+  if (id < 0 || id >= (int)ctx->c.meshes.size() || !ctx->c.meshes[id]) {
+    set_error("invalid mesh id %d", id);
+    return nullptr;
+  }
+  return ctx->c.meshes[id].get();
+}
+
+Batch* get_batch(mqs_ctx* ctx, int id) {
+  if (id < 0 || id >= (int)ctx->c.batches.size() || !ctx->c.batches[id]) {
+    set_error("invalid batch id %d", id);
+    return nullptr;
+  }
+  return ctx->c.batches[id].get();
+}
+
+// Lane-tile width L and cluster size C for `lanes` lanes over n rows:
+// the widest tile that still lets the tiles (with clusters of up to 16 CTAs)
+// cover every SM, then the cluster size that gives about two CTAs per SM.
+void choose_shape(const Ctx& c, int lanes, int n, int precision, int max_L, int& L, int& C) {
+  const int forced_L = env_int("MQS_TILE_L", 0);
+  const int forced_C = env_int("MQS_CLUSTER", 0);
+  const int target = 2 * c.n_sm;
+  L = 1;
+  for (int cand = 32; cand >= 1; cand >>= 1) {
+    if (cand > max_L) continue;
+    const int tiles = (lanes + cand - 1) / cand;
+    if ((int64_t)tiles * 16 >= c.n_sm || cand == 1) {
+      L = cand;
+      break;
+    }
+  }
+  if (forced_L > 0 && forced_L <= max_L) L = forced_L;
+  const int tiles = (lanes + L - 1) / L;
+  const int cmax = max_cluster(L, precision, c.n_sm);
+  C = (target + tiles - 1) / tiles;
+  // at least one full pass of row slots per CTA
+  const int rows_pass = team_threads() / L;
+  const int c_rows = std::max(1, n / rows_pass);
+  C = std::min(C, std::min(cmax, c_rows));
+  if (forced_C > 0) C = std::min(forced_C, cmax);
+  C = std::max(1, C);
+}
+
+ValueSet* value_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool mixed, int& rc) {
+  rc = MQS_OK;
+  ValueSet* vs = nullptr;
+  for (auto& v : b.vsets)
+    if (v->dt == dt) vs = v.get();
+  const int64_t nnz = m.nnz;
+  const cudaStream_t st = ctx->c.stream;
+  if (!vs) {
+    b.vsets.emplace_back(new ValueSet());
+    vs = b.vsets.back().get();
+    vs->dt = dt;
+    if ((rc = vs->A.ensure((size_t)nnz * b.n * sizeof(double))) != MQS_OK) return nullptr;
+    if ((rc = vs->Dinv.ensure((size_t)m.n_free * b.n * sizeof(double))) != MQS_OK) return nullptr;
+    rc = expand_values(m, b.params.as<double>(), b.n, b.n_params, dt, b.n, vs->A.as<double>(),
+                       nullptr, nullptr, nullptr, vs->Dinv.as<double>(), nullptr, b.n, st);
+    if (rc != MQS_OK) return nullptr;
+  }
+  if (mixed && !vs->A32.p) {
+    if ((rc = vs->A32.ensure((size_t)nnz * b.n * sizeof(float))) != MQS_OK) return nullptr;
+    rc = expand_values(m, b.params.as<double>(), b.n, b.n_params, dt, b.n, nullptr, nullptr,
+                       nullptr, vs->A32.as<float>(), nullptr, nullptr, b.n, st);
+    if (rc != MQS_OK) return nullptr;
+  }
+  return vs;
+}
+
+int ensure_mk(mqs_ctx* ctx, Batch& b, const MeshDev& m) {
+  const cudaStream_t st = ctx->c.stream;
+  if (!b.have_M) {
+    MQS_TRY(b.Mv.ensure((size_t)m.nnz * b.n * sizeof(double)));
+    MQS_TRY(expand_values(m, b.params.as<double>(), b.n, b.n_params, 1.0, b.n, nullptr,
+                          b.Mv.as<double>(), nullptr, nullptr, nullptr, nullptr, b.n, st));
+    b.have_M = true;
+  }
+  if (b.qoi_kind == MQS_QOI_ENERGY && !b.have_K) {
+    MQS_TRY(b.Kv.ensure((size_t)m.nnz * b.n * sizeof(double)));
+    MQS_TRY(expand_values(m, b.params.as<double>(), b.n, b.n_params, 1.0, b.n, nullptr, nullptr,
+                          b.Kv.as<double>(), nullptr, nullptr, nullptr, b.n, st));
+    b.have_K = true;
+  }
+  return MQS_OK;
+}
+
+TileDesc make_tile(const LaneSet& ls, int lane0, int n_active, const ValueSet& v, const Batch& b,
+                   int value_col, int per_lane_values, double dt, int n_steps, int init_from_a0,
+                   bool mixed) {
+  TileDesc t;
+  memset(&t, 0, sizeof(t));
+  t.A = v.A.as<double>() + value_col;
+  t.M = b.Mv.as<double>() + value_col;
+  t.K = b.have_K && b.qoi_kind == MQS_QOI_ENERGY ? b.Kv.as<double>() + value_col : nullptr;
+  t.A32 = mixed ? v.A32.as<float>() + value_col : nullptr;
+  t.Dinv = v.Dinv.as<double>() + value_col;
+  t.vs = b.n;
+  t.ds = b.n;
+  t.ls = per_lane_values;
+  t.lane0 = lane0;
+  t.a0 = ls.vec(V_A0) + lane0;
+  t.a1 = ls.vec(V_A1) + lane0;
+  t.y = ls.vec(V_Y) + lane0;
+  t.r = ls.vec(V_R) + lane0;
+  t.p = ls.vec(V_P) + lane0;
+  t.q = ls.vec(V_Q) + lane0;
+  t.z = ls.vec(V_Z) + lane0;
+  t.b = mixed ? ls.vec(V_B) + lane0 : nullptr;
+  t.p32 = mixed ? ls.vec32(W_P32) + lane0 : nullptr;
+  t.q32 = mixed ? ls.vec32(W_Q32) + lane0 : nullptr;
+  t.xs = ls.xs;
+  t.dt = dt;
+  t.t0 = b.t0;
+  t.n_steps = n_steps;
+  t.n_active = n_active;
+  t.init_from_a0 = init_from_a0;
+  return t;
+}
+
+int upload_tiles(mqs_ctx* ctx, LaneSet& ls) {
+  MQS_TRY(ls.tiles.ensure(std::max<size_t>(1, ls.host_tiles.size()) * sizeof(TileDesc)));
+  if (!ls.host_tiles.empty())
+    MQS_CUDA_TRY(cudaMemcpyAsync(ls.tiles.p, ls.host_tiles.data(),
+                                 ls.host_tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                                 ctx->c.stream));
+  return MQS_OK;
+}
+
+TeamConst team_const(const MeshDev& m, const Batch& b, const LaneSet& ls, double cg_tol,
+                     int cg_max) {
+  TeamConst kc;
+  memset(&kc, 0, sizeof(kc));
+  kc.rowptr = m.rowptr.as<int32_t>();
+  kc.colidx = m.colidx.as<int32_t>();
+  kc.F = m.F.as<double>();
+  kc.n = m.n_free;
+  kc.n_phases = m.n_phases;
+  kc.qoi_kind = b.qoi_kind;
+  kc.max_it = cg_max;
+  kc.replace_every = kReplaceEvery;
+  kc.tol2 = cg_tol * cg_tol;
+  kc.omega = kTwoPi * b.freq;
+  kc.lanes = ls.arrays();
+  return kc;
+}
+
+int steps_of(double T, double dt, int& n_steps) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) {
+    set_error("step size must be positive and finite (got %g)", dt);
+    return MQS_EINVAL;
+  }
+  const double q = T / dt;
+  const double r = std::nearbyint(q);
+  if (r < 1.0 || std::fabs(q - r) > 1e-9 * std::max(1.0, r) || r > 2e9) {
+    set_error("(t_end - t0) / dt = %.12g is not a positive integer", q);
+    return MQS_EINVAL;
+  }
+  n_steps = (int)r;
+  return MQS_OK;
+}
+
+double qoi_scale(int kind, int n_steps, double dt) {
+  return kind == MQS_QOI_JOULE ? 1.0 / ((double)n_steps * dt) : 1.0 / (double)n_steps;
+}
+
+// Sequential solves: `segments` sets of n lanes each (fine, and coarse if vc).
+int run_plain(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet* vf, int nsf,
+              const ValueSet* vc, int nsc, int precision, double cg_tol, int cg_max) {
+  const bool mixed = precision == MQS_MIXED;
+  const int nf = vf ? b.n : 0, nc = vc ? b.n : 0;
+  int L, C;
+  choose_shape(ctx->c, nf + nc, m.n_free, precision, 32, L, C);
+  b.nf_pad = (int)round_up(nf, L);
+  b.nc_pad = (int)round_up(nc, L);
+  const int64_t xs = b.nf_pad + b.nc_pad;
+  LaneSet& ls = b.plain;
+  MQS_TRY(ls.ensure((int)xs, xs, m.n_free, mixed));
+  const cudaStream_t st = ctx->c.stream;
+  MQS_CUDA_TRY(cudaMemsetAsync(ls.k0.p, 0, xs * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(ls.qraw.p, 0, xs * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(ls.status.p, 0, xs * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(ls.iters.p, 0, xs * sizeof(double), st));
+  ls.host_tiles.clear();
+  if (nf) {
+    MQS_TRY(lane_sources(b.params.as<double>(), b.n, b.n_params, m.n_regions, m.n_phases, 1,
+                         ls.amp.as<double>(), ls.phi.as<double>(), st));
+    for (int l0 = 0; l0 < nf; l0 += L)
+      ls.host_tiles.push_back(make_tile(ls, l0, std::min(L, nf - l0), *vf, b, l0, 1, vf->dt, nsf,
+                                        0, mixed));
+  }
+  if (nc) {
+    MQS_TRY(lane_sources(b.params.as<double>(), b.n, b.n_params, m.n_regions, m.n_phases, 1,
+                         ls.amp.as<double>() + (size_t)b.nf_pad * kMaxPhases,
+                         ls.phi.as<double>() + (size_t)b.nf_pad * kMaxPhases, st));
+    for (int l0 = 0; l0 < nc; l0 += L)
+      ls.host_tiles.push_back(make_tile(ls, b.nf_pad + l0, std::min(L, nc - l0), *vc, b, l0, 1,
+                                        vc->dt, nsc, 0, mixed));
+  }
+  MQS_TRY(upload_tiles(ctx, ls));
+  const TeamConst kc = team_const(m, b, ls, cg_tol, cg_max);
+  MQS_TRY(launch_propagate(ls.tiles.as<TileDesc>(), (int)ls.host_tiles.size(), L, C, precision,
+                           kc, st));
+  b.stats[1] += (double)nf * nsf + (double)nc * nsc;
+  b.stats[2] += (double)nf * nsf + (double)nc * nsc;
+  return MQS_OK;
+}
+
+int sum_host(mqs_ctx* ctx, const DevBuf& buf, int64_t count, double& out) {
+  std::vector<double> h((size_t)count);
+  if (count)
+    MQS_CUDA_TRY(cudaMemcpyAsync(h.data(), buf.p, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->c.stream));
+  MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  out = 0.0;
+  for (double v : h) out += v;
+  return MQS_OK;
+}
+
+int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
+                 const ValueSet& vcoarse, int n_steps, int M, int cf, int max_iters, double tol,
+                 int precision, double cg_tol, int cg_max, int& iters_out) {
+  const bool mixed = precision == MQS_MIXED;
+  const cudaStream_t st = ctx->c.stream;
+  const int S = n_steps / M, Sc = S / cf;
+  const int ns = b.n;
+  const int lanes = ns * M;
+  int maxL = 1;
+  while (maxL * 2 <= 32 && M % (maxL * 2) == 0) maxL *= 2;
+  int Lf, Cf;
+  choose_shape(ctx->c, lanes, m.n_free, precision, maxL, Lf, Cf);
+  LaneSet& pf = b.par;
+  MQS_TRY(pf.ensure(lanes, lanes, m.n_free, mixed));
+  int Lc, Cc;
+  choose_shape(ctx->c, ns, m.n_free, precision, 32, Lc, Cc);
+  const int64_t xs_c = round_up(ns, Lc);
+  LaneSet& pc = b.chain;
+  MQS_TRY(pc.ensure((int)xs_c, xs_c, m.n_free, mixed));
+  const size_t field = (size_t)m.n_free * lanes * sizeof(double);
+  MQS_TRY(b.U.ensure(field));
+  MQS_TRY(b.G.ensure(field));
+  MQS_TRY(b.jump2.ensure((size_t)ns * M * sizeof(double)));
+  MQS_TRY(b.norm2.ensure((size_t)ns * M * sizeof(double)));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.U.p, 0, field, st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.G.p, 0, field, st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.norm2.p, 0, (size_t)ns * M * sizeof(double), st));
+  // fine lanes: lane = sample * M + slice, k0 = slice * S
+  MQS_TRY(lane_sources(b.params.as<double>(), ns, b.n_params, m.n_regions, m.n_phases, M,
+                       pf.amp.as<double>(), pf.phi.as<double>(), st));
+  MQS_TRY(fill_k0(pf.k0.as<int32_t>(), lanes, M, S, st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pf.qraw.p, 0, lanes * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pf.status.p, 0, lanes * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pf.iters.p, 0, lanes * sizeof(double), st));
+  // chain lanes: one per sample
+  MQS_TRY(lane_sources(b.params.as<double>(), ns, b.n_params, m.n_regions, m.n_phases, 1,
+                       pc.amp.as<double>(), pc.phi.as<double>(), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pc.k0.p, 0, xs_c * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pc.status.p, 0, xs_c * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(pc.iters.p, 0, xs_c * sizeof(double), st));
+  pc.host_tiles.clear();
+  for (int l0 = 0; l0 < ns; l0 += Lc)
+    pc.host_tiles.push_back(make_tile(pc, l0, std::min(Lc, ns - l0), vcoarse, b, l0, 1,
+                                      vcoarse.dt, Sc, 1, mixed));
+  MQS_TRY(upload_tiles(ctx, pc));
+  const TeamConst kcc = team_const(m, b, pc, cg_tol, cg_max);
+  ChainDesc ch;
+  ch.U = b.U.as<double>();
+  ch.E = pf.vec(V_A0);
+  ch.G = b.G.as<double>();
+  ch.xs_par = lanes;
+  ch.M = M;
+  ch.steps_per_slice = Sc;
+  ch.jump2 = b.jump2.as<double>();
+  ch.norm2 = b.norm2.as<double>();
+  // k = 0: coarse sweep
+  ch.s_begin = 0;
+  ch.first_sweep = 1;
+  MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)ns * M * sizeof(double), st));
+  MQS_TRY(launch_chain(pc.tiles.as<TileDesc>(), (int)pc.host_tiles.size(), Lc, Cc, precision,
+                       kcc, ch, st));
+  double exec_steps = (double)ns * (M - 1) * Sc;
+  std::vector<double> hj((size_t)ns * M), hn((size_t)ns * M);
+  int k = 0;
+  for (k = 1; k <= max_iters; ++k) {
+    // fine propagation of slices k-1 .. M-1 (pruned at tile granularity)
+    MQS_TRY(copy_lanes(b.U.as<double>(), pf.vec(V_A0), m.n_free, lanes, 0, lanes, 0, 0, st));
+    pf.host_tiles.clear();
+    for (int s = 0; s < ns; ++s)
+      for (int j0 = 0; j0 < M; j0 += Lf) {
+        if (j0 + Lf <= k - 1) continue;
+        pf.host_tiles.push_back(make_tile(pf, s * M + j0, Lf, vf, b, s, 0, vf.dt, S, 1, mixed));
+        exec_steps += (double)Lf * S;
+      }
+    MQS_TRY(upload_tiles(ctx, pf));
+    const TeamConst kcf = team_const(m, b, pf, cg_tol, cg_max);
+    MQS_TRY(launch_propagate(pf.tiles.as<TileDesc>(), (int)pf.host_tiles.size(), Lf, Cf,
+                             precision, kcf, st));
+    // coarse sweep with the Eq. 12 correction on slices k-1 .. M-2
+    MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)ns * M * sizeof(double), st));
+    if (k - 1 <= M - 2) {
+      ch.s_begin = k - 1;
+      ch.first_sweep = 0;
+      MQS_TRY(launch_chain(pc.tiles.as<TileDesc>(), (int)pc.host_tiles.size(), Lc, Cc, precision,
+                           kcc, ch, st));
+      exec_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
+    }
+    MQS_CUDA_TRY(cudaMemcpyAsync(hj.data(), b.jump2.p, hj.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    MQS_CUDA_TRY(cudaMemcpyAsync(hn.data(), b.norm2.p, hn.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    MQS_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int s = 0; s < ns; ++s) {
+      double num = 0.0, den = 0.0;
+      for (int j = 0; j < M; ++j) {
+        num = std::max(num, std::sqrt(hj[(size_t)s * M + j]));
+        den = std::max(den, std::sqrt(hn[(size_t)s * M + j]));
+      }
+      const double jump = den > 0.0 ? num / den : num;
+      if (!(jump <= tol)) all = false;
+    }
+    if (all || k >= M) break;
+  }
+  iters_out = std::min(k, max_iters);
+  b.stats[1] += exec_steps;
+  b.stats[2] += (double)ns * n_steps;
+  return MQS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mqs_last_error(void) { return g_err.c_str(); }
+
+int mqs_create(mqs_ctx** out, int device, void* cuda_stream) {
+  clear_error();
+  if (!out) {
+    set_error("null output pointer");
+    return MQS_EINVAL;
+  }
+  int count = 0;
+  MQS_CUDA_TRY(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) {
+    set_error("device %d out of range (%d devices)", device, count);
+    return MQS_EINVAL;
+  }
+  MQS_CUDA_TRY(cudaSetDevice(device));
+  int major = 0;
+  MQS_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+  if (major < 9) {
+    set_error("device %d has compute capability %d.x; thread-block clusters need >= 9.0",
+              device, major);
+    return MQS_EINVAL;
+  }
+  auto* ctx = new (std::nothrow) mqs_ctx();
+  if (!ctx) {
+    set_error("out of host memory");
+    return MQS_ENOMEM;
+  }
+  ctx->c.device = device;
+  ctx->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&ctx->c.n_sm, cudaDevAttrMultiProcessorCount, device);
+  *out = ctx;
+  return MQS_OK;
+}
+
+int mqs_set_stream(mqs_ctx* ctx, void* cuda_stream) {
+  MQS_TRY(enter(ctx));
+  ctx->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  return MQS_OK;
+}
+
+int mqs_destroy(mqs_ctx* ctx) {
+  if (!ctx) return MQS_OK;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  delete ctx;
+  return MQS_OK;
+}
+
+int mqs_upload_mesh(mqs_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_tri,
+                    const int32_t* tri, const int32_t* region, int32_t n_regions,
+                    const uint8_t* dirichlet, const int32_t* src_phase, const double* src_coef,
+                    int32_t n_phases, int32_t* mesh_id) {
+  MQS_TRY(enter(ctx));
+  if (!xy || !tri || !region || !dirichlet || !src_phase || !src_coef || !mesh_id) {
+    set_error("null array argument");
+    return MQS_EINVAL;
+  }
+  if (n_nodes < 3 || n_tri < 1 || n_regions < 1 || n_regions > kMaxRegions || n_phases < 0 ||
+      n_phases > kMaxPhases || (int64_t)n_tri * 9 >= (int64_t)INT32_MAX) {
+    set_error("bad mesh sizes: nodes %d, triangles %d, regions %d, phases %d", n_nodes, n_tri,
+              n_regions, n_phases);
+    return MQS_EINVAL;
+  }
+  for (int64_t e = 0; e < n_tri; ++e) {
+    for (int v = 0; v < 3; ++v)
+      if (tri[3 * e + v] < 0 || tri[3 * e + v] >= n_nodes) {
+        set_error("triangle %lld has node id %d out of range", (long long)e, tri[3 * e + v]);
+        return MQS_EINVAL;
+      }
+    if (region[e] < 0 || region[e] >= n_regions) {
+      set_error("triangle %lld has region %d out of range", (long long)e, region[e]);
+      return MQS_EINVAL;
+    }
+    if (src_phase[e] < -1 || src_phase[e] >= n_phases) {
+      set_error("triangle %lld has source phase %d out of range", (long long)e, src_phase[e]);
+      return MQS_EINVAL;
+    }
+    const double* p0 = xy + 2 * (int64_t)tri[3 * e];
+    const double* p1 = xy + 2 * (int64_t)tri[3 * e + 1];
+    const double* p2 = xy + 2 * (int64_t)tri[3 * e + 2];
+    const double d = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]);
+    if (!(std::fabs(d) > 0.0) || !std::isfinite(d)) {
+      set_error("triangle %lld is degenerate", (long long)e);
+      return MQS_EINVAL;
+    }
+  }
+  auto mesh = std::unique_ptr<MeshDev>(new MeshDev());
+  MeshDev& m = *mesh;
+  m.n_nodes = n_nodes;
+  m.n_tri = n_tri;
+  m.n_regions = n_regions;
+  m.n_phases = n_phases;
+  std::vector<int32_t> fid(n_nodes, -1);
+  for (int32_t v = 0; v < n_nodes; ++v)
+    if (!dirichlet[v]) {
+      fid[v] = (int32_t)m.free_node.size();
+      m.free_node.push_back(v);
+    }
+  m.n_free = (int32_t)m.free_node.size();
+  if (m.n_free == 0) {
+    set_error("mesh has no free node");
+    return MQS_EINVAL;
+  }
+  // CSR pattern over free unknowns: couplings through shared triangles
+  std::vector<std::vector<int32_t>> nbr(m.n_free);
+  for (int64_t e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t fa = fid[tri[3 * e + a]];
+      if (fa < 0) continue;
+      for (int bb = 0; bb < 3; ++bb) {
+        const int32_t fb = fid[tri[3 * e + bb]];
+        if (fb >= 0) nbr[fa].push_back(fb);
+      }
+    }
+  std::vector<int32_t> rowptr(m.n_free + 1, 0), colidx, diag(m.n_free);
+  for (int32_t i = 0; i < m.n_free; ++i) {
+    auto& v = nbr[i];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    if ((int)v.size() > kMaxRowNnz) {
+      set_error("free node %d has %zu couplings (limit %d)", m.free_node[i], v.size(), kMaxRowNnz);
+      return MQS_EINVAL;
+    }
+    m.max_row_nnz = std::max<int32_t>(m.max_row_nnz, (int32_t)v.size());
+    rowptr[i + 1] = rowptr[i] + (int32_t)v.size();
+    diag[i] = rowptr[i] + (int32_t)(std::lower_bound(v.begin(), v.end(), i) - v.begin());
+    colidx.insert(colidx.end(), v.begin(), v.end());
+  }
+  m.nnz = (int64_t)colidx.size();
+  // element contributions per nonzero, sorted by (nonzero, code)
+  std::vector<std::pair<int32_t, int32_t>> kc;
+  kc.reserve((size_t)n_tri * 9);
+  for (int64_t e = 0; e < n_tri; ++e)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t fa = fid[tri[3 * e + a]];
+      if (fa < 0) continue;
+      for (int bb = 0; bb < 3; ++bb) {
+        const int32_t fb = fid[tri[3 * e + bb]];
+        if (fb < 0) continue;
+        const int32_t* beg = colidx.data() + rowptr[fa];
+        const int32_t* end = colidx.data() + rowptr[fa + 1];
+        const int32_t k = (int32_t)(std::lower_bound(beg, end, fb) - colidx.data());
+        kc.emplace_back(k, (int32_t)(e * 9 + a * 3 + bb));
+      }
+    }
+  std::sort(kc.begin(), kc.end());
+  std::vector<int32_t> cptr(m.nnz + 1, 0), contrib(kc.size());
+  for (size_t j = 0; j < kc.size(); ++j) {
+    cptr[kc[j].first + 1]++;
+    contrib[j] = kc[j].second;
+  }
+  for (int64_t k = 0; k < m.nnz; ++k) cptr[k + 1] += cptr[k];
+  // source triangles per free row, sorted by (row, triangle)
+  std::vector<std::pair<int32_t, int32_t>> rl;
+  for (int64_t e = 0; e < n_tri; ++e) {
+    if (src_phase[e] < 0) continue;
+    for (int a = 0; a < 3; ++a) {
+      const int32_t fa = fid[tri[3 * e + a]];
+      if (fa >= 0) rl.emplace_back(fa, (int32_t)e);
+    }
+  }
+  std::sort(rl.begin(), rl.end());
+  std::vector<int32_t> lptr(m.n_free + 1, 0), load(rl.size());
+  for (size_t j = 0; j < rl.size(); ++j) {
+    lptr[rl[j].first + 1]++;
+    load[j] = rl[j].second;
+  }
+  for (int32_t i = 0; i < m.n_free; ++i) lptr[i + 1] += lptr[i];
+  const cudaStream_t st = ctx->c.stream;
+  MQS_TRY(m.rowptr.ensure(rowptr.size() * sizeof(int32_t)));
+  MQS_TRY(m.colidx.ensure(colidx.size() * sizeof(int32_t)));
+  MQS_TRY(m.diag.ensure(diag.size() * sizeof(int32_t)));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.rowptr.p, rowptr.data(), rowptr.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.colidx.p, colidx.data(), colidx.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.diag.p, diag.data(), diag.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  MQS_TRY(assemble_region_matrices(m, xy, tri, region, src_phase, src_coef, cptr, contrib, lptr,
+                                   load, st));
+  ctx->c.meshes.push_back(std::move(mesh));
+  *mesh_id = (int32_t)ctx->c.meshes.size() - 1;
+  return MQS_OK;
+}
+
+int mqs_mesh_info(mqs_ctx* ctx, int32_t mesh_id, int32_t* n_free, int64_t* nnz) {
+  MQS_TRY(enter(ctx));
+  MeshDev* m = get_mesh(ctx, mesh_id);
+  if (!m) return MQS_EINVAL;
+  if (n_free) *n_free = m->n_free;
+  if (nnz) *nnz = m->nnz;
+  return MQS_OK;
+}
+
+int mqs_set_samples(mqs_ctx* ctx, int32_t mesh_id, int32_t n_samples, int32_t n_params,
+                    const double* params, int32_t* batch_id) {
+  MQS_TRY(enter(ctx));
+  MeshDev* m = get_mesh(ctx, mesh_id);
+  if (!m) return MQS_EINVAL;
+  if (!params || !batch_id || n_samples < 1) {
+    set_error("need n_samples >= 1, params and batch_id");
+    return MQS_EINVAL;
+  }
+  const int expect = 2 * m->n_regions + 1 + 2 * m->n_phases;
+  if (n_params != expect) {
+    set_error("n_params = %d, the mesh needs 2R + 1 + 2P = %d", n_params, expect);
+    return MQS_EINVAL;
+  }
+  auto b = std::unique_ptr<Batch>(new Batch());
+  b->mesh_id = mesh_id;
+  b->n = n_samples;
+  b->n_params = n_params;
+  const size_t bytes = (size_t)n_samples * n_params * sizeof(double);
+  MQS_TRY(b->params.ensure(bytes));
+  MQS_CUDA_TRY(cudaMemcpyAsync(b->params.p, params, bytes, cudaMemcpyDefault, ctx->c.stream));
+  MQS_TRY(b->qoi.ensure((size_t)n_samples * 2 * sizeof(double)));
+  MQS_TRY(b->status.ensure((size_t)n_samples * sizeof(int32_t)));
+  MQS_CUDA_TRY(cudaMemsetAsync(b->qoi.p, 0, (size_t)n_samples * 2 * sizeof(double), ctx->c.stream));
+  MQS_CUDA_TRY(cudaMemsetAsync(b->status.p, 0, (size_t)n_samples * sizeof(int32_t), ctx->c.stream));
+  if (!is_device_ptr(params)) MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  m->live_batches++;
+  ctx->c.batches.push_back(std::move(b));
+  *batch_id = (int32_t)ctx->c.batches.size() - 1;
+  return MQS_OK;
+}
+
+int mqs_set_time(mqs_ctx* ctx, int32_t batch_id, double t0, double t_end, double freq_hz,
+                 int32_t qoi_kind) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  if (!(t_end > t0) || !std::isfinite(t0) || !std::isfinite(t_end) || !std::isfinite(freq_hz) ||
+      (qoi_kind != MQS_QOI_ENERGY && qoi_kind != MQS_QOI_JOULE)) {
+    set_error("bad time window [%g, %g], frequency %g or QoI kind %d", t0, t_end, freq_hz,
+              qoi_kind);
+    return MQS_EINVAL;
+  }
+  b->t0 = t0;
+  b->t_end = t_end;
+  b->freq = freq_hz;
+  b->qoi_kind = qoi_kind;
+  b->time_set = true;
+  return MQS_OK;
+}
+
+int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level, double dt_prev,
+                  int32_t n_slices, int32_t coarse_factor, int32_t max_par_iters, double par_tol,
+                  int32_t precision, double cg_tol, int32_t cg_max_iters, int32_t* par_iters_out) {
+  MQS_TRY(enter(ctx));
+  Batch* bp = get_batch(ctx, batch_id);
+  if (!bp) return MQS_EINVAL;
+  Batch& b = *bp;
+  MeshDev& m = *ctx->c.meshes[b.mesh_id];
+  if (!b.time_set) {
+    set_error("mqs_set_time must be called before mqs_propagate");
+    return MQS_EINVAL;
+  }
+  if ((precision != MQS_FP64 && precision != MQS_MIXED) || cg_max_iters < 1 || !(cg_tol >= 0.0) ||
+      n_slices < 1 || level < 0 || dt_prev < 0.0) {
+    set_error("bad precision %d, cg_tol %g, cg_max_iters %d, n_slices %d, level %d or dt_prev %g",
+              precision, cg_tol, cg_max_iters, n_slices, level, dt_prev);
+    return MQS_EINVAL;
+  }
+  const double T = b.t_end - b.t0;
+  int nsf = 0, nsc = 0;
+  MQS_TRY(steps_of(T, dt_level, nsf));
+  if (dt_prev > 0.0) MQS_TRY(steps_of(T, dt_prev, nsc));
+  if (n_slices > 1) {
+    if (coarse_factor < 1 || nsf % n_slices || (nsf / n_slices) % coarse_factor ||
+        max_par_iters < 1 || max_par_iters > n_slices || !(par_tol >= 0.0)) {
+      set_error("Parareal needs steps (%d) divisible by slices (%d) times coarse_factor (%d) "
+                "and 1 <= max_par_iters <= slices",
+                nsf, n_slices, coarse_factor);
+      return MQS_EINVAL;
+    }
+  }
+  const bool mixed = precision == MQS_MIXED;
+  MQS_TRY(ensure_mk(ctx, b, m));
+  int rc = MQS_OK;
+  ValueSet* vf = value_set(ctx, b, m, dt_level, mixed, rc);
+  if (!vf) return rc;
+  ValueSet* vc = nullptr;
+  if (dt_prev > 0.0) {
+    vc = value_set(ctx, b, m, dt_prev, mixed, rc);
+    if (!vc) return rc;
+  }
+  b.level = level;
+  b.has_coarse = vc != nullptr;
+  for (double& s : b.stats) s = 0.0;
+  b.stats[3] = m.n_free;
+  const cudaStream_t st = ctx->c.stream;
+  int par_iters = 0;
+  if (n_slices == 1) {
+    MQS_TRY(run_plain(ctx, b, m, vf, nsf, vc, nsc, precision, cg_tol, cg_max_iters));
+    b.mode = 1;
+    b.M = 1;
+    MQS_TRY(finish_qoi(b.plain.qraw.as<double>(),
+                       vc ? b.plain.qraw.as<double>() + b.nf_pad : nullptr, b.n, 1,
+                       qoi_scale(b.qoi_kind, nsf, dt_level),
+                       vc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
+    MQS_CUDA_TRY(cudaMemsetAsync(b.status.p, 0, (size_t)b.n * sizeof(int32_t), st));
+  } else {
+    // companion level-(l-1) solve first (sequential), then Parareal on level l
+    if (vc) MQS_TRY(run_plain(ctx, b, m, nullptr, 0, vc, nsc, precision, cg_tol, cg_max_iters));
+    ValueSet* vC = value_set(ctx, b, m, dt_level * coarse_factor, mixed, rc);
+    if (!vC) return rc;
+    MQS_TRY(run_parareal(ctx, b, m, *vf, *vC, nsf, n_slices, coarse_factor, max_par_iters,
+                         par_tol, precision, cg_tol, cg_max_iters, par_iters));
+    b.mode = 2;
+    b.M = n_slices;
+    MQS_TRY(finish_qoi(b.par.qraw.as<double>(), vc ? b.plain.qraw.as<double>() : nullptr, b.n,
+                       n_slices, qoi_scale(b.qoi_kind, nsf, dt_level),
+                       vc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
+    MQS_CUDA_TRY(cudaMemsetAsync(b.status.p, 0, (size_t)b.n * sizeof(int32_t), st));
+  }
+  if (par_iters_out) *par_iters_out = par_iters;
+  return MQS_OK;
+}
+
+int mqs_read_qoi(mqs_ctx* ctx, int32_t batch_id, double* qoi, int32_t* status) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  if (!qoi) {
+    set_error("null qoi array");
+    return MQS_EINVAL;
+  }
+  const cudaStream_t st = ctx->c.stream;
+  MQS_CUDA_TRY(cudaMemcpyAsync(qoi, b->qoi.p, (size_t)b->n * 2 * sizeof(double), cudaMemcpyDefault,
+                               st));
+  if (status) {
+    // or the per-lane status bits of every solve of the sample
+    std::vector<int32_t> out((size_t)b->n, 0);
+    auto fold = [&](const LaneSet& ls, int lanes, int lps, int off) -> int {
+      std::vector<int32_t> h((size_t)lanes);
+      MQS_CUDA_TRY(cudaMemcpyAsync(h.data(), ls.status.as<int32_t>() + off, lanes * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, st));
+      MQS_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int l = 0; l < lanes; ++l) out[l / lps] |= h[l];
+      return MQS_OK;
+    };
+    if (b->mode == 1) {
+      MQS_TRY(fold(b->plain, b->n, 1, 0));
+      if (b->has_coarse) MQS_TRY(fold(b->plain, b->n, 1, b->nf_pad));
+    } else if (b->mode == 2) {
+      MQS_TRY(fold(b->par, b->n * b->M, b->M, 0));
+      MQS_TRY(fold(b->chain, b->n, 1, 0));
+      if (b->has_coarse) MQS_TRY(fold(b->plain, b->n, 1, 0));
+    }
+    MQS_CUDA_TRY(cudaMemcpyAsync(status, out.data(), out.size() * sizeof(int32_t),
+                                 cudaMemcpyDefault, st));
+  }
+  MQS_CUDA_TRY(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  if (!a || (which != 0 && which != 1) || b->mode == 0 || (which == 1 && !b->has_coarse)) {
+    set_error("no such state (which = %d)", which);
+    return MQS_EINVAL;
+  }
+  const MeshDev& m = *ctx->c.meshes[b->mesh_id];
+  const cudaStream_t st = ctx->c.stream;
+  const bool dev = is_device_ptr(a);
+  DevBuf tmp;
+  double* out = a;
+  if (!dev) {
+    MQS_TRY(tmp.ensure((size_t)b->n * m.n_free * sizeof(double)));
+    out = tmp.as<double>();
+  }
+  if (which == 0 && b->mode == 2) {
+    MQS_TRY(transpose_to_rows(b->par.vec(V_A0), b->par.xs, m.n_free, b->n, b->M, b->M - 1, out, st));
+  } else if (which == 0) {
+    MQS_TRY(transpose_to_rows(b->plain.vec(V_A0), b->plain.xs, m.n_free, b->n, 1, 0, out, st));
+  } else {
+    const int off = b->mode == 2 ? 0 : b->nf_pad;
+    MQS_TRY(transpose_to_rows(b->plain.vec(V_A0), b->plain.xs, m.n_free, b->n, 1, off, out, st));
+  }
+  if (!dev)
+    MQS_CUDA_TRY(cudaMemcpyAsync(a, out, (size_t)b->n * m.n_free * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  MQS_CUDA_TRY(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b || !stats) return MQS_EINVAL;
+  double it = 0.0, t;
+  if (b->mode == 1) {
+    MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
+    it += t;
+  } else if (b->mode == 2) {
+    MQS_TRY(sum_host(ctx, b->par.iters, b->par.lanes, t));
+    it += t;
+    MQS_TRY(sum_host(ctx, b->chain.iters, b->chain.xs, t));
+    it += t;
+    if (b->has_coarse) {
+      MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
+      it += t;
+    }
+  }
+  b->stats[0] = it;
+  memcpy(stats, b->stats, sizeof(b->stats));
+  return MQS_OK;
+}
+
+int mqs_apply(mqs_ctx* ctx, int32_t batch_id, int32_t which, double dt, const double* x,
+              double* y) {
+  MQS_TRY(enter(ctx));
+  Batch* bp = get_batch(ctx, batch_id);
+  if (!bp) return MQS_EINVAL;
+  Batch& b = *bp;
+  if (!x || !y || which < 0 || which > 2) {
+    set_error("bad arguments to mqs_apply");
+    return MQS_EINVAL;
+  }
+  const MeshDev& m = *ctx->c.meshes[b.mesh_id];
+  const cudaStream_t st = ctx->c.stream;
+  const int saved_kind = b.qoi_kind;
+  if (which == 1) b.qoi_kind = MQS_QOI_ENERGY;   // build K values
+  int rc = ensure_mk(ctx, b, m);
+  b.qoi_kind = saved_kind;
+  if (rc != MQS_OK) return rc;
+  const double* vals = nullptr;
+  if (which == 0) vals = b.Mv.as<double>();
+  if (which == 1) vals = b.Kv.as<double>();
+  if (which == 2) {
+    ValueSet* v = value_set(ctx, b, m, dt, false, rc);
+    if (!v) return rc;
+    vals = v->A.as<double>();
+  }
+  const size_t bytes = (size_t)b.n * m.n_free * sizeof(double);
+  DevBuf dx, dy;
+  const double* xin = x;
+  double* yout = y;
+  if (!is_device_ptr(x)) {
+    MQS_TRY(dx.ensure(bytes));
+    MQS_CUDA_TRY(cudaMemcpyAsync(dx.p, x, bytes, cudaMemcpyHostToDevice, st));
+    xin = dx.as<double>();
+  }
+  const bool ydev = is_device_ptr(y);
+  if (!ydev) {
+    MQS_TRY(dy.ensure(bytes));
+    yout = dy.as<double>();
+  }
+  MQS_TRY(batched_spmv(m, vals, b.n, b.n, xin, yout, st));
+  if (!ydev) MQS_CUDA_TRY(cudaMemcpyAsync(y, yout, bytes, cudaMemcpyDeviceToHost, st));
+  MQS_CUDA_TRY(cudaStreamSynchronize(st));
+  return MQS_OK;
+}
+
+int mqs_mlmc_reset(mqs_ctx* ctx, int32_t n_levels) {
+  MQS_TRY(enter(ctx));
+  if (n_levels < 1 || n_levels > 64) {
+    set_error("n_levels = %d out of range [1, 64]", n_levels);
+    return MQS_EINVAL;
+  }
+  MQS_TRY(ctx->c.mlmc.ensure((size_t)n_levels * 4 * sizeof(double)));
+  MQS_CUDA_TRY(cudaMemsetAsync(ctx->c.mlmc.p, 0, (size_t)n_levels * 4 * sizeof(double),
+                               ctx->c.stream));
+  ctx->c.n_levels = n_levels;
+  return MQS_OK;
+}
+
+int mqs_mlmc_accumulate(mqs_ctx* ctx, int32_t batch_id, int32_t level) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  if (level < 0 || level >= ctx->c.n_levels || b->mode == 0) {
+    set_error("level %d outside the %d reset levels, or batch not propagated", level,
+              ctx->c.n_levels);
+    return MQS_EINVAL;
+  }
+  return mlmc_accumulate_dev(b->qoi.as<double>(), b->n, level,
+                             ctx->c.mlmc.as<double>() + 4 * level, ctx->c.stream);
+}
+
+int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rmse) {
+  MQS_TRY(enter(ctx));
+  if (ctx->c.n_levels < 1) {
+    set_error("mqs_mlmc_reset was not called");
+    return MQS_EINVAL;
+  }
+  std::vector<double> rec((size_t)ctx->c.n_levels * 4);
+  MQS_CUDA_TRY(cudaMemcpyAsync(rec.data(), ctx->c.mlmc.p, rec.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->c.stream));
+  MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  double est = 0.0, var_sum = 0.0;
+  for (int l = 0; l < ctx->c.n_levels; ++l) {
+    const double n = rec[4 * l], mean = rec[4 * l + 1], m2 = rec[4 * l + 2];
+    const double var = n > 1.0 ? m2 / (n - 1.0) : 0.0;
+    if (levels) {
+      levels[3 * l] = n;
+      levels[3 * l + 1] = mean;
+      levels[3 * l + 2] = var;
+    }
+    est += mean;
+    if (n > 0.0) var_sum += var / n;
+  }
+  if (estimate) *estimate = est;
+  if (rmse) *rmse = std::sqrt(var_sum);
+  return MQS_OK;
+}
+
+int mqs_free_batch(mqs_ctx* ctx, int32_t batch_id) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  ctx->c.meshes[b->mesh_id]->live_batches--;
+  ctx->c.batches[batch_id].reset();
+  return MQS_OK;
+}
+
+int mqs_free_mesh(mqs_ctx* ctx, int32_t mesh_id) {
+  MQS_TRY(enter(ctx));
+  MeshDev* m = get_mesh(ctx, mesh_id);
+  if (!m) return MQS_EINVAL;
+  if (m->live_batches > 0) {
+    set_error("mesh %d still has %d live batches", mesh_id, m->live_batches);
+    return MQS_EINVAL;
+  }
+  MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  ctx->c.meshes[mesh_id].reset();
+  return MQS_OK;
+}
+
+}  // extern "C"

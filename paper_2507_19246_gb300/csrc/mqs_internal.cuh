@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "mqs.h"
+
+namespace mqs {
+
+constexpr int kMaxRegions = 16;
+constexpr int kMaxPhases = 4;
+constexpr int kMaxRowNnz = 32;
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define MQS_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::mqs::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                       __FILE__, __LINE__);                                        \
+      return MQS_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+#define MQS_TRY(expr)             \
+  do {                            \
+    int s_ = (expr);              \
+    if (s_ != MQS_OK) return s_;  \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffer
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // (Re)allocate to at least `n` bytes; contents undefined.
+  int ensure(size_t n) {
+    if (n <= bytes && p) return MQS_OK;
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMalloc(%zu bytes) failed: %s", n, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MQS_ENOMEM : MQS_ECUDA;
+    }
+    bytes = n;
+    return MQS_OK;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- mesh
+struct MeshDev {
+  int32_t n_nodes = 0, n_tri = 0, n_regions = 0, n_phases = 0;
+  int32_t n_free = 0;
+  int64_t nnz = 0;
+  int32_t max_row_nnz = 0;
+  DevBuf rowptr, colidx, diag;   // CSR pattern over free unknowns (int32)
+  DevBuf Mr, Kr;                 // [R][nnz] region reference matrices (double)
+  DevBuf F;                      // [P][n_free] per-phase load vectors (double)
+  std::vector<int32_t> free_node;
+  int live_batches = 0;
+};
+
+// ---------------------------------------------------------------- solve lanes
+// One tile = L consecutive lanes that share a step size and a step count and
+// are advanced together by one cluster ("team") of CTAs.
+struct TileDesc {
+  // matrix values of lane l of this tile: element k at vals[k * vs + l * ls]
+  const double* A;
+  const double* M;
+  const double* K;       // stiffness values (energy QoI only, else nullptr)
+  const float* A32;      // FP32 copy of A (mixed precision only)
+  const double* Dinv;    // inverse diagonal of A: row i at Dinv[i * ds + l * ls]
+  int64_t vs, ds;
+  int32_t ls;            // 1: per-lane values, 0: one value column for the tile
+  int32_t lane0;         // first lane of the tile in the batch-wide lane arrays
+  // lane vectors: element (i, l) at v[i * xs + l]; pointers include the tile offset
+  double *a0, *a1, *y, *r, *p, *q, *z, *b;
+  float *p32, *q32;
+  int64_t xs;
+  double dt, t0;
+  int32_t n_steps;
+  int32_t n_active;      // lanes [0, n_active) of the tile are real
+  int32_t init_from_a0;  // 1: a0 holds the initial state, 0: start from zero
+  int32_t pad_;
+};
+
+// per-lane data in batch-wide arrays (index = lane0 + l)
+struct LaneArrays {
+  const double* src_amp;   // [lanes][kMaxPhases]  J0 * amp_p
+  const double* src_phi;   // [lanes][kMaxPhases]  phase_p
+  const int32_t* k0;       // [lanes] global index of the first step
+  double* qoi_raw;         // [lanes] raw QoI sum
+  int32_t* status;         // [lanes] MQS_ST_* bits (or-ed)
+  double* iters;           // [lanes] total PCG iterations (accumulated)
+};
+
+struct TeamConst {
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const double* F;         // [P][n]
+  int32_t n;
+  int32_t n_phases;
+  int32_t qoi_kind;
+  int32_t max_it;
+  int32_t replace_every;   // mixed precision: FP64 residual replacement period
+  int32_t pad_;
+  double tol2;             // cg_tol^2
+  double omega;            // 2 pi f
+  LaneArrays lanes;
+};
+
+// Parareal coarse chain: lane l of the chain is sample (chain_lane0 + l);
+// slice state arrays are in the fine-batch lane layout (lane = sample * M + s).
+struct ChainDesc {
+  double *U, *E, *G;       // [n][xs_par] slice starts, fine ends, previous coarse ends
+  int64_t xs_par;
+  int32_t M;               // slices per sample
+  int32_t s_begin;         // first slice whose coarse propagation runs
+  int32_t steps_per_slice; // coarse steps per slice
+  int32_t first_sweep;     // 1: k = 0 sweep (no correction)
+  double* jump2;           // [samples][M] ||U_new[s] - U_old[s]||^2 (s = slice start index)
+  double* norm2;           // [samples][M] ||U[s]||^2
+};
+
+// launchers (mqs_team.cu)
+int launch_propagate(const TileDesc* d_tiles, int n_tiles, int L, int C, int precision,
+                     const TeamConst& kc, cudaStream_t st);
+int launch_chain(const TileDesc* d_tiles, int n_tiles, int L, int C, int precision,
+                 const TeamConst& kc, const ChainDesc& ch, cudaStream_t st);
+int team_threads();
+int max_cluster(int L, int precision, int n_sm);
+
+// setup kernels (mqs_setup.cu)
+int assemble_region_matrices(MeshDev& m, const double* xy, const int32_t* tri,
+                             const int32_t* region, const int32_t* src_phase,
+                             const double* src_coef, const std::vector<int32_t>& contrib_ptr,
+                             const std::vector<int32_t>& contrib, const std::vector<int32_t>& load_ptr,
+                             const std::vector<int32_t>& load, cudaStream_t st);
+int expand_values(const MeshDev& m, const double* params, int n_samples, int n_params,
+                  double dt, int64_t vs, double* A, double* M, double* K, float* A32,
+                  double* Dinv, float* Dinv32, int64_t ds, cudaStream_t st);
+int lane_sources(const double* params, int n_samples, int n_params, int n_regions,
+                 int n_phases, int lanes_per_sample, double* src_amp, double* src_phi,
+                 cudaStream_t st);
+int batched_spmv(const MeshDev& m, const double* vals, int64_t vs, int n_samples,
+                 const double* x, double* y, cudaStream_t st);
+
+// small kernels (mqs_stats.cu)
+int fill_k0(int32_t* k0, int n, int lanes_per_sample, int steps_per_slice, cudaStream_t st);
+int copy_lanes(const double* src, double* dst, int64_t n, int64_t xs, int lane_begin,
+               int lane_end, int lanes_per_sample, int slice_begin, cudaStream_t st);
+int transpose_to_rows(const double* lanes, int64_t xs, int n, int n_samples, int lane_stride,
+                      int lane_offset, double* out, cudaStream_t st);
+int transpose_from_rows(const double* rows, int n, int n_samples, double* lanes, int64_t xs,
+                        cudaStream_t st);
+int finish_qoi(const double* raw_fine, const double* raw_coarse, int n_samples, int lanes_per_sample,
+               double scale_fine, double scale_coarse, double* qoi, cudaStream_t st);
+int mlmc_accumulate_dev(const double* qoi, int n_samples, int level, double* record,
+                        cudaStream_t st);
+
+}  // namespace mqs

@@ -1,0 +1,298 @@
+"""Python binding of the C ABI in ``include/mqs.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_lib/libmqs.so``.  The module-level functions carry the C names
+(``mqs_create``, ``mqs_upload_mesh``, ...); ``Context`` wraps them with
+handles and numpy / torch arrays.  Arrays may be numpy arrays (host) or CUDA
+torch tensors (device); device tensors are passed as raw device pointers.
+
+The library must be built first (``__graft_entry__.build()`` or
+``python -m paper_2507_19246_gb300.build``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MQS_OK, MQS_EINVAL, MQS_ENOMEM, MQS_ECUDA, MQS_ENOTCONV = 0, -1, -2, -3, -4
+MQS_FP64, MQS_MIXED = 0, 1
+MQS_QOI_ENERGY, MQS_QOI_JOULE = 0, 1
+MQS_ST_NOTCONV, MQS_ST_NONFINITE = 1, 2
+
+_lib = None
+_P = C.c_void_p
+_i32, _i64, _f64 = C.c_int32, C.c_int64, C.c_double
+
+_SIGS = {
+    "mqs_last_error": (C.c_char_p, []),
+    "mqs_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "mqs_set_stream": (C.c_int, [_P, _P]),
+    "mqs_destroy": (C.c_int, [_P]),
+    "mqs_upload_mesh": (C.c_int, [_P, _i32, _P, _i32, _P, _P, _i32, _P, _P, _P, _i32,
+                                  C.POINTER(_i32)]),
+    "mqs_mesh_info": (C.c_int, [_P, _i32, C.POINTER(_i32), C.POINTER(_i64)]),
+    "mqs_set_samples": (C.c_int, [_P, _i32, _i32, _i32, _P, C.POINTER(_i32)]),
+    "mqs_set_time": (C.c_int, [_P, _i32, _f64, _f64, _f64, _i32]),
+    "mqs_propagate": (C.c_int, [_P, _i32, _i32, _f64, _f64, _i32, _i32, _i32, _f64, _i32, _f64,
+                                _i32, C.POINTER(_i32)]),
+    "mqs_read_qoi": (C.c_int, [_P, _i32, _P, _P]),
+    "mqs_read_state": (C.c_int, [_P, _i32, _i32, _P]),
+    "mqs_read_stats": (C.c_int, [_P, _i32, _P]),
+    "mqs_apply": (C.c_int, [_P, _i32, _i32, _f64, _P, _P]),
+    "mqs_mlmc_reset": (C.c_int, [_P, _i32]),
+    "mqs_mlmc_accumulate": (C.c_int, [_P, _i32, _i32]),
+    "mqs_mlmc_readout": (C.c_int, [_P, _P, C.POINTER(_f64), C.POINTER(_f64)]),
+    "mqs_free_batch": (C.c_int, [_P, _i32]),
+    "mqs_free_mesh": (C.c_int, [_P, _i32]),
+}
+
+
+class MQSError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} returned {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmqs.so (built in-tree); raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(fn, code):
+    if code != MQS_OK:
+        raise MQSError(fn, code, load().mqs_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (host or CUDA)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+# ----------------------------------------------------------------- C names
+def mqs_last_error() -> str:
+    return load().mqs_last_error().decode(errors="replace")
+
+
+def mqs_create(device: int = 0, stream: int = None) -> int:
+    h = _P()
+    _check("mqs_create", load().mqs_create(C.byref(h), device, stream))
+    return h.value
+
+
+def mqs_set_stream(ctx, stream):
+    _check("mqs_set_stream", load().mqs_set_stream(ctx, stream))
+
+
+def mqs_destroy(ctx):
+    _check("mqs_destroy", load().mqs_destroy(ctx))
+
+
+def mqs_upload_mesh(ctx, mesh) -> int:
+    xy = _host(mesh.xy, np.float64)
+    tri = _host(mesh.tri, np.int32)
+    reg = _host(mesh.region, np.int32)
+    dr = _host(mesh.dirichlet, np.uint8)
+    ph = _host(mesh.src_phase, np.int32)
+    cf = _host(mesh.src_coef, np.float64)
+    out = _i32()
+    _check("mqs_upload_mesh", load().mqs_upload_mesh(
+        ctx, xy.shape[0], _ptr(xy), tri.shape[0], _ptr(tri), _ptr(reg), mesh.n_regions, _ptr(dr),
+        _ptr(ph), _ptr(cf), mesh.n_phases, C.byref(out)))
+    return out.value
+
+
+def mqs_mesh_info(ctx, mesh_id):
+    n, z = _i32(), _i64()
+    _check("mqs_mesh_info", load().mqs_mesh_info(ctx, mesh_id, C.byref(n), C.byref(z)))
+    return n.value, z.value
+
+
+def mqs_set_samples(ctx, mesh_id, params) -> int:
+    if isinstance(params, np.ndarray) or not hasattr(params, "data_ptr"):
+        params = _host(params, np.float64)
+    ns, npar = params.shape
+    out = _i32()
+    _check("mqs_set_samples", load().mqs_set_samples(ctx, mesh_id, ns, npar, _ptr(params),
+                                                     C.byref(out)))
+    return out.value
+
+
+def mqs_set_time(ctx, batch, t0, t_end, freq_hz, qoi_kind):
+    _check("mqs_set_time", load().mqs_set_time(ctx, batch, t0, t_end, freq_hz, qoi_kind))
+
+
+def mqs_propagate(ctx, batch, level, dt_level, dt_prev=0.0, n_slices=1, coarse_factor=1,
+                  max_par_iters=1, par_tol=0.0, precision=MQS_FP64, cg_tol=1e-12,
+                  cg_max_iters=5000) -> int:
+    it = _i32()
+    _check("mqs_propagate", load().mqs_propagate(
+        ctx, batch, level, dt_level, dt_prev, n_slices, coarse_factor, max_par_iters, par_tol,
+        precision, cg_tol, cg_max_iters, C.byref(it)))
+    return it.value
+
+
+def mqs_read_qoi(ctx, batch, qoi, status=None):
+    _check("mqs_read_qoi", load().mqs_read_qoi(ctx, batch, _ptr(qoi), _ptr(status)))
+
+
+def mqs_read_state(ctx, batch, which, a):
+    _check("mqs_read_state", load().mqs_read_state(ctx, batch, which, _ptr(a)))
+
+
+def mqs_read_stats(ctx, batch):
+    s = np.zeros(4)
+    _check("mqs_read_stats", load().mqs_read_stats(ctx, batch, _ptr(s)))
+    return s
+
+
+def mqs_apply(ctx, batch, which, dt, x, y):
+    _check("mqs_apply", load().mqs_apply(ctx, batch, which, dt, _ptr(x), _ptr(y)))
+
+
+def mqs_mlmc_reset(ctx, n_levels):
+    _check("mqs_mlmc_reset", load().mqs_mlmc_reset(ctx, n_levels))
+
+
+def mqs_mlmc_accumulate(ctx, batch, level):
+    _check("mqs_mlmc_accumulate", load().mqs_mlmc_accumulate(ctx, batch, level))
+
+
+def mqs_mlmc_readout(ctx, n_levels):
+    lv = np.zeros((n_levels, 3))
+    est, rmse = _f64(), _f64()
+    _check("mqs_mlmc_readout", load().mqs_mlmc_readout(ctx, _ptr(lv), C.byref(est), C.byref(rmse)))
+    return lv, est.value, rmse.value
+
+
+def mqs_free_batch(ctx, batch):
+    _check("mqs_free_batch", load().mqs_free_batch(ctx, batch))
+
+
+def mqs_free_mesh(ctx, mesh_id):
+    _check("mqs_free_mesh", load().mqs_free_mesh(ctx, mesh_id))
+
+
+# ----------------------------------------------------------------- convenience
+class Context:
+    """A library context on one GPU; methods mirror the C entry points."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = None
+        self.h = mqs_create(device, stream)
+        self._n = {}
+
+    def close(self):
+        if self.h:
+            mqs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        mqs_set_stream(self.h, stream)
+
+    def upload_mesh(self, mesh) -> int:
+        return mqs_upload_mesh(self.h, mesh)
+
+    def mesh_info(self, mesh_id):
+        return mqs_mesh_info(self.h, mesh_id)
+
+    def set_samples(self, mesh_id, params) -> int:
+        b = mqs_set_samples(self.h, mesh_id, params)
+        self._n[b] = (mesh_id, int(params.shape[0]))
+        return b
+
+    def set_time(self, batch, t0, t_end, freq_hz=50.0, qoi_kind=MQS_QOI_JOULE):
+        mqs_set_time(self.h, batch, t0, t_end, freq_hz, qoi_kind)
+
+    def propagate(self, batch, level, dt_level, **kw) -> int:
+        return mqs_propagate(self.h, batch, level, dt_level, **kw)
+
+    def read_qoi(self, batch):
+        ns = self._n[batch][1]
+        q = np.zeros((ns, 2))
+        st = np.zeros(ns, dtype=np.int32)
+        mqs_read_qoi(self.h, batch, q, st)
+        return q, st
+
+    def read_state(self, batch, which=0):
+        mesh_id, ns = self._n[batch]
+        n, _ = self.mesh_info(mesh_id)
+        a = np.zeros((ns, n))
+        mqs_read_state(self.h, batch, which, a)
+        return a
+
+    def read_stats(self, batch):
+        return mqs_read_stats(self.h, batch)
+
+    def apply(self, batch, which, dt, x):
+        x = _host(x, np.float64)
+        y = np.zeros_like(x)
+        mqs_apply(self.h, batch, which, dt, x, y)
+        return y
+
+    def mlmc_reset(self, n_levels):
+        self._levels = n_levels
+        mqs_mlmc_reset(self.h, n_levels)
+
+    def mlmc_accumulate(self, batch, level):
+        mqs_mlmc_accumulate(self.h, batch, level)
+
+    def mlmc_readout(self):
+        return mqs_mlmc_readout(self.h, self._levels)
+
+    def free_batch(self, batch):
+        mqs_free_batch(self.h, batch)
+        self._n.pop(batch, None)
+
+    def free_mesh(self, mesh_id):
+        mqs_free_mesh(self.h, mesh_id)
