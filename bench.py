@@ -1,0 +1,374 @@
+"""Benchmark: sample-DoF-steps/s of the GPU implicit-Euler / Parareal path.
+
+Default workload (the configuration the metric is quoted on that fits one
+GPU): Parareal on one nominal sample of the 20k-node annulus in FP64 -- fine
+dt = period/512 over 8 periods (4096 steps), coarse dt = 64 fine, 64 slices,
+relative jump tolerance 1e-8, joule-loss QoI.  One bench step is one full
+pass of the path on that input: per-sample value expansion, the Parareal
+iterations (fine batches + coarse sweeps with the fused correction), the QoI
+and the MLMC moment update, read back to device memory.  Throughput counts
+serial-equivalent fine steps: 4096 x 19584 sample-DoF-steps per solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precision fp64|mixed] [--workload parareal20k|mcsquare]
+
+With N > 1 (torchrun) every rank runs an independent replica ("replicas
+only": the Parareal solve of one sample has no cross-GPU exchange); value is
+the units of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ workloads
+def workload(name):
+    from workloads import configs, meshes, params
+    if name == "parareal20k":
+        c = configs.PARAREAL_ANNULUS
+        return dict(name="parareal_annulus20k", mesh=meshes.annulus("20k"),
+                    params=params.annulus_nominal(1), t_end=c.periods * configs.PERIOD,
+                    dt=c.dt, n_steps=c.n_steps, n_slices=c.n_slices, cf=c.coarse_factor,
+                    par_tol=c.tol, qoi=c.qoi, cg_tol=1e-12)
+    if name == "parareal20k_short":
+        # profiling case: the same mesh, lanes and launch shapes as parareal20k
+        # but 4 fine steps per slice (coarse step = 4 fine steps), so that one
+        # launch of each kernel ends in well under a second
+        c = configs.PARAREAL_ANNULUS
+        return dict(name="parareal_annulus20k_short", mesh=meshes.annulus("20k"),
+                    params=params.annulus_nominal(1), t_end=256 * c.dt, dt=c.dt, n_steps=256,
+                    n_slices=c.n_slices, cf=4, par_tol=c.tol, qoi=c.qoi, cg_tol=1e-12)
+    if name == "mcsquare":
+        c = configs.MC_SQUARE
+        return dict(name="mc_square16", mesh=meshes.unit_square(16),
+                    params=params.square_samples(c.n_samples), t_end=c.t_end,
+                    dt=c.t_end / c.n_steps, n_steps=c.n_steps, n_slices=1, cf=1, par_tol=0.0,
+                    qoi=c.qoi, cg_tol=1e-13)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                s, m = float(f[0]), float(f[1])
+            except Exception:
+                continue
+            sm.append(s)
+            mx = m
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm if mx and s > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ bytes model
+def algorithmic_bytes(n_free, nnz, lane_iters, lane_steps, lanes_per_value, precision):
+    """Algorithmic DRAM bytes of the stepping kernel (per launch set).
+
+    Per lane and CG iteration, each row moves its matrix row (z/n values plus
+    the inverse diagonal, shared by `lanes_per_value` lanes) and 12 lane-vector
+    words: SpMV reads p, writes q; the update reads x, p, r, q and writes
+    x, r, z; the direction update reads z, p and writes p.  Per lane and
+    step, the right-hand side and the QoI add two matrix rows and 10 words.
+    Mixed precision: FP32 values and FP32 p/q copies in the SpMV.
+    """
+    zn = nnz / n_free
+    wv = 4 if precision == "mixed" else 8
+    per_it = (wv * zn + 8) / lanes_per_value + 12 * 8
+    if precision == "mixed":
+        per_it += 2 * 4 - 8  # p32 written, q32 in place of q; SpMV reads p32
+    per_step = 2 * 8 * zn / lanes_per_value + 10 * 8
+    return n_free * (lane_iters * per_it + lane_steps * per_step)
+
+
+# ------------------------------------------------------------------ oracle arm
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import fem, stepper
+from workloads import meshes, params, configs
+mesh = meshes.{mesh_fn}
+p = {params_expr}
+n_steps = {n_steps}
+t0 = time.perf_counter()
+d = fem.Discretisation(mesh, p[0])
+prop = stepper.ImplicitEuler(d, {dt!r})
+a, raw, _ = prop.run(np.zeros(d.n), n_steps, qoi={qoi})
+el = time.perf_counter() - t0
+print(json.dumps({{"seconds": el, "units": n_steps * d.n}}))
+"""
+
+
+def oracle_sample(wl, n_steps):
+    """Time the oracle's serial fine propagator on `n_steps` steps of the
+    workload's first sample in a single-threaded subprocess."""
+    mesh_fn = {"parareal_annulus20k": "annulus('20k')", "parareal_annulus20k_short": "annulus('20k')",
+               "mc_square16": "unit_square(16)"}[wl["name"]]
+    params_expr = ("params.annulus_nominal(1)" if wl["name"].startswith("parareal")
+                   else "params.square_samples(1)")
+    code = ORACLE_SNIPPET.format(root=ROOT, mesh_fn=mesh_fn, params_expr=params_expr,
+                                 n_steps=n_steps, dt=wl["dt"], qoi=wl["qoi"])
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["units"] / r["seconds"], r["seconds"]
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    n_steps = 256 if wl["name"].startswith("parareal") else wl["n_steps"]
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, _ = oracle_sample(wl, n_steps)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    sample = (f"serial fine implicit-Euler propagator of the oracle, {n_steps} of "
+              f"{wl['n_steps']} steps of the workload's sample per bench step, 1 thread")
+    line = {"impl": "reference", "metric": "sample-DoF-steps/s", "value": value,
+            "unit": "sample-DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"]},
+            "e2e": {"value": value, "unit": "sample-DoF-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": "sample-DoF-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": sample}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, wl, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2507_19246_gb300 import mqs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    prec = mqs.MQS_MIXED if args.precision == "mixed" else mqs.MQS_FP64
+    ctx = mqs.Context(dev, stream.cuda_stream)
+    mesh_id = ctx.upload_mesh(wl["mesh"])
+    n_free, nnz = ctx.mesh_info(mesh_id)
+    p_host = torch.from_numpy(wl["params"]).pin_memory()
+    p_dev = p_host.to(f"cuda:{dev}")
+    ns = p_host.shape[0]
+    q_dev = torch.zeros((ns, 2), dtype=torch.float64, device=f"cuda:{dev}")
+    q_host = torch.zeros((ns, 2), dtype=torch.float64).pin_memory()
+    flush = torch.empty(int(512e6) // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    lanes_per_value = 1
+
+    def one_step(params_src, qoi_dst):
+        b = mqs.mqs_set_samples(ctx.h, mesh_id, params_src)
+        mqs.mqs_set_time(ctx.h, b, 0.0, wl["t_end"], 50.0, wl["qoi"])
+        k = mqs.mqs_propagate(ctx.h, b, 0, wl["dt"], 0.0, wl["n_slices"], wl["cf"],
+                              wl["n_slices"], wl["par_tol"], prec, wl["cg_tol"], 20000)
+        mqs.mqs_mlmc_accumulate(ctx.h, b, 0)
+        mqs.mqs_read_qoi(ctx.h, b, qoi_dst)
+        st = mqs.mqs_read_stats(ctx.h, b)
+        mqs.mqs_free_batch(ctx.h, b)
+        return k, st
+
+    mqs.mqs_mlmc_reset(ctx.h, 1)
+    for _ in range(args.warmup):
+        one_step(p_dev, q_dev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    # ---- device-resident timed region
+    times, ks, stats = [], [], []
+    launches0 = ctx.profile_read()[0]
+    ctx.profile(True)
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            k, st = one_step(p_dev, q_dev)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            ks.append(k)
+            stats.append(st)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = int(prof[0] - launches0)
+    torch.cuda.synchronize()
+    # ---- end-to-end through the public API from pinned host memory
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_step(p_host, q_host.numpy())
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+    q = q_dev.cpu().numpy()
+    # ---- max over ranks
+    ms_total = sum(times)
+    if dist:
+        t = torch.tensor([ms_total, sum(e2e_times)], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total, e2e_total = t.tolist()
+    else:
+        e2e_total = sum(e2e_times)
+    units = float(ns) * wl["n_steps"] * n_free           # serial-equivalent sample-DoF-steps
+    value = world * units * args.steps / (ms_total / 1e3)
+    e2e_value = world * units * len(e2e_times) / (e2e_total / 1e3)
+    if rank != 0:
+        return
+    st = stats[-1]
+    # roofline of the dominant kernel (stepping kernel vs coarse sweep), from the
+    # live CUDA-event timings of the timed region and the bytes model
+    step_ms, step_n, sweep_ms, sweep_n = prof[2], prof[1], prof[4], prof[3]
+    lpv = 1
+    if wl["n_slices"] > 1:
+        # Parareal fine lanes share one sample's values per tile
+        lpv = 32 if wl["n_slices"] % 32 == 0 else wl["n_slices"]
+    step_bytes = sum(algorithmic_bytes(n_free, nnz, s[4], s[6], lpv, args.precision)
+                     for s in stats)
+    sweep_bytes = sum(algorithmic_bytes(n_free, nnz, s[5], s[7], 1, args.precision) for s in stats)
+    peaks, peak_kind = _peaks()
+    dominant = "stepping" if step_ms >= sweep_ms else "coarse_sweep"
+    d_ms, d_n, d_bytes = (step_ms, step_n, step_bytes) if dominant == "stepping" else \
+        (sweep_ms, sweep_n, sweep_bytes)
+    achieved = (d_bytes / max(d_n, 1)) / (d_ms / max(d_n, 1) / 1e3) / 1e9 if d_ms > 0 else 0.0
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    try:
+        tr = json.load(open(traffic_path)).get(f"{wl['name']}:{args.precision}:{dominant}")
+        traffic = tr
+    except Exception:
+        pass
+    # CPU baseline: the oracle's serial fine propagator on a bounded sample
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_cpu = 768 if wl["name"].startswith("parareal") else wl["n_steps"]
+        cv, secs = oracle_sample(wl, n_cpu)
+        cpu = {"value": cv, "unit": "sample-DoF-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_cpu} of {wl['n_steps']} fine steps of the workload's sample, serial "
+                         f"implicit Euler with banded Cholesky ({secs:.1f} s, 1 thread)"}
+    clocks = clk.summary()
+    line = {
+        "metric": "sample-DoF-steps/s", "value": value, "unit": "sample-DoF-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "mesh": wl["mesh"].name, "n_free": n_free, "nnz": nnz,
+                   "samples": ns, "steps": wl["n_steps"], "dt": wl["dt"],
+                   "slices": wl["n_slices"], "coarse_factor": wl["cf"],
+                   "parareal_tol": wl["par_tol"], "cg_tol": wl["cg_tol"],
+                   "precision": args.precision, "parareal_iters": ks[-1],
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": statistics.median(times), "p99_ms": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
+        "time_to_solution_s": ms_total / args.steps / 1e3,
+        "cg_iters_per_lane_step": (st[0] / max(st[1], 1)),
+        "effort_solve_steps": st[1], "serial_equivalent_solve_steps": st[2],
+        "qoi": float(q[0, 0]),
+        "e2e": {"value": e2e_value, "unit": "sample-DoF-steps/s",
+                "h2d_bytes_per_step": int(p_host.numel() * 8), "d2h_bytes_per_step": int(ns * 2 * 8)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "kernel_ms": {"stepping": step_ms / args.steps, "coarse_sweep": sweep_ms / args.steps}},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, wl, rank, world, dist)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

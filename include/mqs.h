@@ -148,11 +148,25 @@ int mqs_read_qoi(mqs_ctx* ctx, int32_t batch_id, double* qoi, int32_t* status);
  * unknowns in increasing node id. */
 int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a);
 
-/* Solver counters of the last propagate: stats[0] = total PCG iterations of
- * all lanes, stats[1] = implicit-Euler solve-steps executed (Parareal counts
- * every executed fine and coarse step), stats[2] = serial-equivalent
- * solve-steps, stats[3] = DoF count n_free.  Host array of 4. */
+/* Solver counters of the last propagate (host array of MQS_N_STATS):
+ *   [0] PCG iterations summed over all lanes
+ *   [1] implicit-Euler solve-steps executed (Parareal: every fine and coarse step run)
+ *   [2] serial-equivalent solve-steps (the sequential solves this replaces)
+ *   [3] free unknowns n_free
+ *   [4] lane-iterations / [6] lane-steps of the sequential-stepping kernel
+ *   [5] lane-iterations / [7] lane-steps of the Parareal coarse-sweep kernel */
+#define MQS_N_STATS 8
 int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats);
+
+/* Instrumentation.  mqs_profile(ctx, 1) clears and starts recording CUDA-event
+ * timings around every launch of the two time-stepping kernels on the
+ * context's stream; 0 stops.  mqs_profile_read fills out[5] (host):
+ *   [0] kernels launched by this library in this process since it was loaded
+ *   [1] recorded launches / [2] their summed duration (ms) of the stepping kernel
+ *   [3] recorded launches / [4] their summed duration (ms) of the coarse-sweep kernel
+ * and synchronises the stream. */
+int mqs_profile(mqs_ctx* ctx, int32_t enable);
+int mqs_profile_read(mqs_ctx* ctx, double* out);
 
 /* Apply a sample's matrix: y[s] = X_s x[s] with X = M (which = 0), K (1) or
  * A = M/dt + K (2) for every sample s of the batch; x, y host or device,

@@ -4,6 +4,7 @@
 #include "mqs_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -21,6 +22,9 @@ void set_error(const char* fmt, ...) {
   g_err = buf;
 }
 void clear_error() { g_err.clear(); }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches += n; }
 
 namespace {
 
@@ -82,7 +86,7 @@ struct Batch {
   int M = 0;
   DevBuf qoi, status;
   int level = 0;
-  double stats[4] = {0, 0, 0, 0};
+  double stats[MQS_N_STATS] = {};
 };
 
 struct Ctx {
@@ -93,7 +97,36 @@ struct Ctx {
   std::vector<std::unique_ptr<Batch>> batches;
   DevBuf mlmc;
   int n_levels = 0;
+  // instrumentation: event pairs around the stepping (0) and coarse-sweep (1) launches
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
+  size_t ev_used[2] = {0, 0};
+  ~Ctx() {
+    for (auto& v : ev)
+      for (auto& e : v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+  }
 };
+
+// Record the start (begin = true) or end event of a launch of kind k.
+int prof_mark(Ctx& c, int k, bool begin) {
+  if (!c.prof) return MQS_OK;
+  if (begin) {
+    if (c.ev_used[k] == c.ev[k].size()) {
+      cudaEvent_t a, b;
+      MQS_CUDA_TRY(cudaEventCreate(&a));
+      MQS_CUDA_TRY(cudaEventCreate(&b));
+      c.ev[k].emplace_back(a, b);
+    }
+    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].first, c.stream));
+  } else {
+    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].second, c.stream));
+    c.ev_used[k]++;
+  }
+  return MQS_OK;
+}
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -148,32 +181,46 @@ Batch* get_batch(mqs_ctx* ctx, int id) {
   return ctx->c.batches[id].get();
 }
 
-// Lane-tile width L and cluster size C for `lanes` lanes over n rows:
-// the widest tile that still lets the tiles (with clusters of up to 16 CTAs)
-// cover every SM, then the cluster size that gives about two CTAs per SM.
+// Lane-tile width L and cluster size C for `lanes` lanes over n rows.  A team
+// lives for the whole run, so all teams should be resident at once: among the
+// tile widths whose tiles fit the resident cluster count for some C, take the
+// shape that keeps the most CTAs busy (ties: wider tiles), with at least one
+// full pass of row slots per CTA.  When the tiles outnumber the resident
+// clusters even at C = 1, the widest tile and C = 1 are used (several waves).
 void choose_shape(const Ctx& c, int lanes, int n, int precision, int max_L, int& L, int& C) {
   const int forced_L = env_int("MQS_TILE_L", 0);
   const int forced_C = env_int("MQS_CLUSTER", 0);
-  const int target = 2 * c.n_sm;
-  L = 1;
+  int best_L = 0, best_C = 0;
+  int64_t best_busy = -1;
+  int lanes_p2 = 1;
+  while (lanes_p2 < lanes && lanes_p2 < 32) lanes_p2 <<= 1;
   for (int cand = 32; cand >= 1; cand >>= 1) {
-    if (cand > max_L) continue;
+    if (cand > max_L || cand > lanes_p2) continue;
+    if (forced_L > 0 && cand != forced_L) continue;
     const int tiles = (lanes + cand - 1) / cand;
-    if ((int64_t)tiles * 16 >= c.n_sm || cand == 1) {
-      L = cand;
-      break;
+    const int rows_pass = team_threads() / cand;
+    const int c_rows = std::max(1, n / rows_pass);
+    const int cmax = std::min(max_cluster(cand, precision, c.n_sm), c_rows);
+    for (int cc = cmax; cc >= 1; --cc) {
+      if (forced_C > 0 && cc != std::min(forced_C, cmax)) continue;
+      const int active = max_active_clusters(cand, precision, cc);
+      if (active < tiles && !(forced_C > 0)) continue;
+      const int64_t busy = (int64_t)std::min(tiles, std::max(active, 1)) * cc;
+      if (busy > best_busy) {
+        best_busy = busy;
+        best_L = cand;
+        best_C = cc;
+      }
+      break;   // the largest C that fits is the best for this width
     }
   }
-  if (forced_L > 0 && forced_L <= max_L) L = forced_L;
-  const int tiles = (lanes + L - 1) / L;
-  const int cmax = max_cluster(L, precision, c.n_sm);
-  C = (target + tiles - 1) / tiles;
-  // at least one full pass of row slots per CTA
-  const int rows_pass = team_threads() / L;
-  const int c_rows = std::max(1, n / rows_pass);
-  C = std::min(C, std::min(cmax, c_rows));
-  if (forced_C > 0) C = std::min(forced_C, cmax);
-  C = std::max(1, C);
+  if (best_L == 0) {
+    // more tiles than resident clusters: widest tile, single-CTA teams
+    best_L = std::min(std::min(max_L, lanes_p2), forced_L > 0 ? forced_L : 32);
+    best_C = forced_C > 0 ? std::min(forced_C, max_cluster(best_L, precision, c.n_sm)) : 1;
+  }
+  L = best_L;
+  C = std::max(1, best_C);
 }
 
 ValueSet* value_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool mixed, int& rc) {
@@ -333,8 +380,11 @@ int run_plain(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet* vf, int 
   }
   MQS_TRY(upload_tiles(ctx, ls));
   const TeamConst kc = team_const(m, b, ls, cg_tol, cg_max);
+  MQS_TRY(prof_mark(ctx->c, 0, true));
   MQS_TRY(launch_propagate(ls.tiles.as<TileDesc>(), (int)ls.host_tiles.size(), L, C, precision,
                            kc, st));
+  MQS_TRY(prof_mark(ctx->c, 0, false));
+  b.stats[6] += (double)nf * nsf + (double)nc * nsc;
   b.stats[1] += (double)nf * nsf + (double)nc * nsc;
   b.stats[2] += (double)nf * nsf + (double)nc * nsc;
   return MQS_OK;
@@ -410,9 +460,12 @@ int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
   ch.s_begin = 0;
   ch.first_sweep = 1;
   MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)ns * M * sizeof(double), st));
+  MQS_TRY(prof_mark(ctx->c, 1, true));
   MQS_TRY(launch_chain(pc.tiles.as<TileDesc>(), (int)pc.host_tiles.size(), Lc, Cc, precision,
                        kcc, ch, st));
+  MQS_TRY(prof_mark(ctx->c, 1, false));
   double exec_steps = (double)ns * (M - 1) * Sc;
+  double chain_steps = (double)ns * (M - 1) * Sc, fine_steps = 0.0;
   std::vector<double> hj((size_t)ns * M), hn((size_t)ns * M);
   int k = 0;
   for (k = 1; k <= max_iters; ++k) {
@@ -424,19 +477,25 @@ int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
         if (j0 + Lf <= k - 1) continue;
         pf.host_tiles.push_back(make_tile(pf, s * M + j0, Lf, vf, b, s, 0, vf.dt, S, 1, mixed));
         exec_steps += (double)Lf * S;
+        fine_steps += (double)Lf * S;
       }
     MQS_TRY(upload_tiles(ctx, pf));
     const TeamConst kcf = team_const(m, b, pf, cg_tol, cg_max);
+    MQS_TRY(prof_mark(ctx->c, 0, true));
     MQS_TRY(launch_propagate(pf.tiles.as<TileDesc>(), (int)pf.host_tiles.size(), Lf, Cf,
                              precision, kcf, st));
+    MQS_TRY(prof_mark(ctx->c, 0, false));
     // coarse sweep with the Eq. 12 correction on slices k-1 .. M-2
     MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)ns * M * sizeof(double), st));
     if (k - 1 <= M - 2) {
       ch.s_begin = k - 1;
       ch.first_sweep = 0;
+      MQS_TRY(prof_mark(ctx->c, 1, true));
       MQS_TRY(launch_chain(pc.tiles.as<TileDesc>(), (int)pc.host_tiles.size(), Lc, Cc, precision,
                            kcc, ch, st));
+      MQS_TRY(prof_mark(ctx->c, 1, false));
       exec_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
+      chain_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
     }
     MQS_CUDA_TRY(cudaMemcpyAsync(hj.data(), b.jump2.p, hj.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));
@@ -457,6 +516,8 @@ int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
   }
   iters_out = std::min(k, max_iters);
   b.stats[1] += exec_steps;
+  b.stats[6] += fine_steps;
+  b.stats[7] += chain_steps;
   b.stats[2] += (double)ns * n_steps;
   return MQS_OK;
 }
@@ -856,23 +917,54 @@ int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a) {
 int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats) {
   MQS_TRY(enter(ctx));
   Batch* b = get_batch(ctx, batch_id);
-  if (!b || !stats) return MQS_EINVAL;
-  double it = 0.0, t;
-  if (b->mode == 1) {
-    MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
-    it += t;
-  } else if (b->mode == 2) {
-    MQS_TRY(sum_host(ctx, b->par.iters, b->par.lanes, t));
-    it += t;
-    MQS_TRY(sum_host(ctx, b->chain.iters, b->chain.xs, t));
-    it += t;
-    if (b->has_coarse) {
-      MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
-      it += t;
-    }
+  if (!b) return MQS_EINVAL;
+  if (!stats) {
+    set_error("null stats array");
+    return MQS_EINVAL;
   }
-  b->stats[0] = it;
+  double prop = 0.0, chain = 0.0, t;
+  if (b->mode == 1 || b->has_coarse) {
+    MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
+    prop += t;
+  }
+  if (b->mode == 2) {
+    MQS_TRY(sum_host(ctx, b->par.iters, b->par.lanes, t));
+    prop += t;
+    MQS_TRY(sum_host(ctx, b->chain.iters, b->chain.xs, t));
+    chain += t;
+  }
+  b->stats[0] = prop + chain;
+  b->stats[4] = prop;
+  b->stats[5] = chain;
   memcpy(stats, b->stats, sizeof(b->stats));
+  return MQS_OK;
+}
+
+int mqs_profile(mqs_ctx* ctx, int32_t enable) {
+  MQS_TRY(enter(ctx));
+  ctx->c.prof = enable != 0;
+  if (enable) ctx->c.ev_used[0] = ctx->c.ev_used[1] = 0;
+  return MQS_OK;
+}
+
+int mqs_profile_read(mqs_ctx* ctx, double* out) {
+  MQS_TRY(enter(ctx));
+  if (!out) {
+    set_error("null output array");
+    return MQS_EINVAL;
+  }
+  MQS_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+  out[0] = (double)g_launches.load();
+  for (int k = 0; k < 2; ++k) {
+    double ms = 0.0;
+    for (size_t j = 0; j < ctx->c.ev_used[k]; ++j) {
+      float e = 0.0f;
+      MQS_CUDA_TRY(cudaEventElapsedTime(&e, ctx->c.ev[k][j].first, ctx->c.ev[k][j].second));
+      ms += e;
+    }
+    out[1 + 2 * k] = (double)ctx->c.ev_used[k];
+    out[2 + 2 * k] = ms;
+  }
   return MQS_OK;
 }
 

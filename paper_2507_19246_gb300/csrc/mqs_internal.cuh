@@ -142,6 +142,9 @@ struct ChainDesc {
   double* norm2;           // [samples][M] ||U[s]||^2
 };
 
+// process-wide count of kernels launched by the library
+void count_launch(int n = 1);
+
 // launchers (mqs_team.cu)
 int launch_propagate(const TileDesc* d_tiles, int n_tiles, int L, int C, int precision,
                      const TeamConst& kc, cudaStream_t st);
@@ -149,6 +152,7 @@ int launch_chain(const TileDesc* d_tiles, int n_tiles, int L, int C, int precisi
                  const TeamConst& kc, const ChainDesc& ch, cudaStream_t st);
 int team_threads();
 int max_cluster(int L, int precision, int n_sm);
+int max_active_clusters(int L, int precision, int C);
 
 // setup kernels (mqs_setup.cu)
 int assemble_region_matrices(MeshDev& m, const double* xy, const int32_t* tri,

@@ -214,11 +214,13 @@ int assemble_region_matrices(MeshDev& m, const double* xy, const int32_t* tri,
       m.nnz, R, d_xy.as<double>(), d_tri.as<int32_t>(), d_reg.as<int32_t>(),
       d_cptr.as<int32_t>(), d_c.as<int32_t>(), m.Mr.as<double>(), m.Kr.as<double>());
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   if (P > 0) {
     k_load_vectors<<<grid_for(m.n_free, 256), 256, 0, st>>>(
         m.n_free, P, d_xy.as<double>(), d_tri.as<int32_t>(), d_ph.as<int32_t>(),
         d_coef.as<double>(), d_lptr.as<int32_t>(), d_l.as<int32_t>(), m.F.as<double>());
     MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   }
   // the temporary buffers are freed when this returns: wait for the kernels
   MQS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -233,11 +235,13 @@ int expand_values(const MeshDev& m, const double* params, int n_samples, int n_p
   k_expand<<<grid, bx, 0, st>>>(m.nnz, n_samples, m.n_regions, n_params, params, dt,
                                 m.Mr.as<double>(), m.Kr.as<double>(), vs, A, M, K, A32);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   if (Dinv || Dinv32) {
     dim3 g2((unsigned)std::min(m.n_free, 4096), (unsigned)((n_samples + bx - 1) / bx));
     k_inv_diag<<<g2, bx, 0, st>>>(m.n_free, n_samples, m.diag.as<int32_t>(), A, vs, Dinv,
                                   Dinv32, ds);
     MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   }
   return MQS_OK;
 }
@@ -250,6 +254,7 @@ int lane_sources(const double* params, int n_samples, int n_params, int n_region
                                                      n_phases, lanes_per_sample, src_amp,
                                                      src_phi);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
@@ -259,6 +264,7 @@ int batched_spmv(const MeshDev& m, const double* vals, int64_t vs, int n_samples
   k_spmv_rows<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(
       m.n_free, n_samples, m.rowptr.as<int32_t>(), m.colidx.as<int32_t>(), vals, vs, x, y);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 

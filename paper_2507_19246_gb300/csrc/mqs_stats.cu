@@ -126,6 +126,7 @@ unsigned grid_of(int64_t total, int block) {
 int fill_k0(int32_t* k0, int n, int lps, int steps, cudaStream_t st) {
   k_fill_k0<<<grid_of(n, 256), 256, 0, st>>>(k0, n, lps, steps);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
@@ -134,6 +135,7 @@ int copy_lanes(const double* src, double* dst, int64_t n, int64_t xs, int lb, in
   if (le <= lb) return MQS_OK;
   k_copy_lanes<<<grid_of(n * (le - lb), 256), 256, 0, st>>>(src, dst, n, xs, lb, le);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
@@ -141,6 +143,7 @@ int transpose_to_rows(const double* lanes, int64_t xs, int n, int ns, int stride
                       double* out, cudaStream_t st) {
   k_to_rows<<<grid_of((int64_t)n * ns, 256), 256, 0, st>>>(lanes, xs, n, ns, stride, off, out);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
@@ -148,6 +151,7 @@ int transpose_from_rows(const double* rows, int n, int ns, double* lanes, int64_
                         cudaStream_t st) {
   k_from_rows<<<grid_of((int64_t)n * ns, 256), 256, 0, st>>>(rows, n, ns, lanes, xs);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
@@ -155,12 +159,14 @@ int finish_qoi(const double* rf, const double* rc, int ns, int lps, double sf, d
                double* qoi, cudaStream_t st) {
   k_finish_qoi<<<grid_of(ns, 128), 128, 0, st>>>(rf, rc, ns, lps, sf, sc, qoi);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 
 int mlmc_accumulate_dev(const double* qoi, int ns, int, double* rec, cudaStream_t st) {
   k_mlmc_moments<<<1, kMomThreads, 0, st>>>(qoi, ns, rec);
   MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
   return MQS_OK;
 }
 

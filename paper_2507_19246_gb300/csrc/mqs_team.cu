@@ -30,6 +30,8 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 namespace cg = cooperative_groups;
 
 namespace mqs {
@@ -444,6 +446,7 @@ int launch_prop_t(const TileDesc* d_tiles, int n_tiles, int C, const TeamConst& 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   MQS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, d_tiles, kc));
+  count_launch();
   return MQS_OK;
 }
 
@@ -465,11 +468,12 @@ int launch_chain_t(const TileDesc* d_tiles, int n_tiles, int C, const TeamConst&
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   MQS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, d_tiles, kc, ch));
+  count_launch();
   return MQS_OK;
 }
 
 template <class K>
-bool cluster_fits(K kern, int C) {
+int active_clusters(K kern, int C) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * 2));
   cfg.blockDim = dim3(kThreads);
@@ -484,25 +488,52 @@ bool cluster_fits(K kern, int C) {
   if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                    cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
   if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return num > 0;
+  return num;
+}
+
+template <int L, int PREC>
+int active_t(int C) {
+  return std::min(active_clusters(k_propagate<L, PREC>, C), active_clusters(k_chain<L, PREC>, C));
 }
 
 template <int L, int PREC>
 int max_cluster_t() {
   for (int C = 16; C > 1; C /= 2)
-    if (cluster_fits(k_propagate<L, PREC>, C) && cluster_fits(k_chain<L, PREC>, C)) return C;
+    if (active_t<L, PREC>(C) > 0) return C;
   return 1;
 }
 
 }  // namespace
 
 int team_threads() { return kThreads; }
+
+// Number of clusters of size C of the team kernels that can be resident at once.
+int max_active_clusters(int L, int precision, int C) {
+  static int cache[6][2][17] = {};
+  int li = 0;
+  while ((1 << li) < L && li < 5) ++li;
+  const int pi = precision ? 1 : 0;
+  if (C < 1 || C > 16) return 0;
+  if (cache[li][pi][C] == 0) {
+    int v = 0;
+    switch (L) {
+      case 1: v = pi ? active_t<1, 1>(C) : active_t<1, 0>(C); break;
+      case 2: v = pi ? active_t<2, 1>(C) : active_t<2, 0>(C); break;
+      case 4: v = pi ? active_t<4, 1>(C) : active_t<4, 0>(C); break;
+      case 8: v = pi ? active_t<8, 1>(C) : active_t<8, 0>(C); break;
+      case 16: v = pi ? active_t<16, 1>(C) : active_t<16, 0>(C); break;
+      default: v = pi ? active_t<32, 1>(C) : active_t<32, 0>(C); break;
+    }
+    cache[li][pi][C] = v > 0 ? v : -1;
+  }
+  return cache[li][pi][C] > 0 ? cache[li][pi][C] : 0;
+}
 
 // Largest cluster size (16, 8, 4, 2 or 1) both team kernels of this tile
 // width and precision can be launched with; cached per (L, precision).

@@ -46,6 +46,8 @@ _SIGS = {
     "mqs_mlmc_reset": (C.c_int, [_P, _i32]),
     "mqs_mlmc_accumulate": (C.c_int, [_P, _i32, _i32]),
     "mqs_mlmc_readout": (C.c_int, [_P, _P, C.POINTER(_f64), C.POINTER(_f64)]),
+    "mqs_profile": (C.c_int, [_P, _i32]),
+    "mqs_profile_read": (C.c_int, [_P, _P]),
     "mqs_free_batch": (C.c_int, [_P, _i32]),
     "mqs_free_mesh": (C.c_int, [_P, _i32]),
 }
@@ -178,8 +180,11 @@ def mqs_read_state(ctx, batch, which, a):
     _check("mqs_read_state", load().mqs_read_state(ctx, batch, which, _ptr(a)))
 
 
+MQS_N_STATS = 8
+
+
 def mqs_read_stats(ctx, batch):
-    s = np.zeros(4)
+    s = np.zeros(MQS_N_STATS)
     _check("mqs_read_stats", load().mqs_read_stats(ctx, batch, _ptr(s)))
     return s
 
@@ -201,6 +206,16 @@ def mqs_mlmc_readout(ctx, n_levels):
     est, rmse = _f64(), _f64()
     _check("mqs_mlmc_readout", load().mqs_mlmc_readout(ctx, _ptr(lv), C.byref(est), C.byref(rmse)))
     return lv, est.value, rmse.value
+
+
+def mqs_profile(ctx, enable):
+    _check("mqs_profile", load().mqs_profile(ctx, int(bool(enable))))
+
+
+def mqs_profile_read(ctx):
+    out = np.zeros(5)
+    _check("mqs_profile_read", load().mqs_profile_read(ctx, _ptr(out)))
+    return out
 
 
 def mqs_free_batch(ctx, batch):
@@ -289,6 +304,13 @@ class Context:
 
     def mlmc_readout(self):
         return mqs_mlmc_readout(self.h, self._levels)
+
+    def profile(self, enable=True):
+        mqs_profile(self.h, enable)
+
+    def profile_read(self):
+        """[launches, step-kernel launches, ms, sweep-kernel launches, ms]"""
+        return mqs_profile_read(self.h)
 
     def free_batch(self, batch):
         mqs_free_batch(self.h, batch)
