@@ -195,8 +195,8 @@ void choose_shape(const Ctx& c, int lanes, int n, int precision, int max_L, int&
   int lanes_p2 = 1;
   while (lanes_p2 < lanes && lanes_p2 < 32) lanes_p2 <<= 1;
   for (int cand = 32; cand >= 1; cand >>= 1) {
-    if (cand > max_L || cand > lanes_p2) continue;
-    if (forced_L > 0 && cand != forced_L) continue;
+    if (cand > max_L) continue;
+    if (forced_L > 0 ? cand != forced_L : cand > lanes_p2) continue;
     const int tiles = (lanes + cand - 1) / cand;
     const int rows_pass = team_threads() / cand;
     const int c_rows = std::max(1, n / rows_pass);
@@ -216,7 +216,7 @@ void choose_shape(const Ctx& c, int lanes, int n, int precision, int max_L, int&
   }
   if (best_L == 0) {
     // more tiles than resident clusters: widest tile, single-CTA teams
-    best_L = std::min(std::min(max_L, lanes_p2), forced_L > 0 ? forced_L : 32);
+    best_L = std::min(max_L, forced_L > 0 ? forced_L : lanes_p2);
     best_C = forced_C > 0 ? std::min(forced_C, max_cluster(best_L, precision, c.n_sm)) : 1;
   }
   L = best_L;
