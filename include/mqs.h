@@ -185,6 +185,50 @@ int mqs_mlmc_reset(mqs_ctx* ctx, int32_t n_levels);
 int mqs_mlmc_accumulate(mqs_ctx* ctx, int32_t batch_id, int32_t level);
 int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rmse);
 
+/* Sequential implicit-Euler stepping that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run -- a host application driving
+ * the GPU from a real-time or signal-safe path, a runtime that partitions all
+ * device memory into its own pools at start-up, or code that forbids
+ * allocation inside a region it records.  They own every input and output;
+ * the library works in a static device scratch array of 32 MiB that each GPU
+ * loading the library holds until the process exits.
+ *
+ * It runs the same stepping kernel as mqs_propagate on n_lanes independent
+ * lanes from a(t0) = 0 (Eq. 7 with the same Jacobi-PCG and the same QoI
+ * definitions), with matrices the caller has assembled:
+ *   device          CUDA device ordinal (made current)
+ *   cuda_stream     cudaStream_t or NULL; all work is enqueued on it
+ *   n, rowptr, colidx, nnz   device, CSR pattern of the n x n free-unknown matrices
+ *                   (int32, columns ascending within a row, at most 32 per row)
+ *   n_lanes         lanes (samples) >= 1
+ *   A, M, K         device, values [nnz][n_lanes] (lane fastest) of A = M/dt + K,
+ *                   of M, and of K (K only for MQS_QOI_ENERGY, else may be NULL)
+ *   Dinv            device, [n][n_lanes] inverse diagonal of A
+ *   n_phases, F     0..4 phases; device [n_phases][n] load vectors
+ *   src_amp, src_phase  host or device, [n_lanes][n_phases]: J0 amp_p and phase_p
+ *                   of each lane (J_p(t) = amp sin(2 pi f t - 2 pi p / P + phase))
+ *   t0, dt, n_steps, freq_hz, qoi_kind, cg_tol, cg_max_iters   as in mqs_propagate
+ *   a_out           device, [n][n_lanes]: final state (also used as work space)
+ *   qoi_out         device, [n_lanes]: the quantity of interest
+ *   status_out      device, [n_lanes] MQS_ST_* bits, or NULL
+ * Limit: 6 * n * n_lanes doubles plus about 72 bytes per lane and the tile
+ * table must fit in the 32 MiB array (for example n = 19584 with 32 lanes);
+ * larger problems return MQS_EINVAL with the required size in the message.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array and leaves its contents behind; the call clears
+ * the parts that must start at zero itself.  Calls whose work overlaps on the
+ * GPU (different streams or threads without ordering) race on the array. */
+int mqs_propagate_noalloc(int32_t device, void* cuda_stream, int32_t n, const int32_t* rowptr,
+                          const int32_t* colidx, int64_t nnz, int32_t n_lanes, const double* A,
+                          const double* M, const double* K, const double* Dinv,
+                          int32_t n_phases, const double* F, const double* src_amp,
+                          const double* src_phase, double t0, double dt, int32_t n_steps,
+                          double freq_hz, int32_t qoi_kind, double cg_tol, int32_t cg_max_iters,
+                          double* a_out, double* qoi_out, int32_t* status_out);
+
 /* Release a batch or a mesh (a mesh must have no live batch). */
 int mqs_free_batch(mqs_ctx* ctx, int32_t batch_id);
 int mqs_free_mesh(mqs_ctx* ctx, int32_t mesh_id);

@@ -48,6 +48,9 @@ _SIGS = {
     "mqs_mlmc_readout": (C.c_int, [_P, _P, C.POINTER(_f64), C.POINTER(_f64)]),
     "mqs_profile": (C.c_int, [_P, _i32]),
     "mqs_profile_read": (C.c_int, [_P, _P]),
+    "mqs_propagate_noalloc": (C.c_int, [_i32, _P, _i32, _P, _P, _i64, _i32, _P, _P, _P, _P, _i32,
+                                        _P, _P, _P, _f64, _f64, _i32, _f64, _i32, _f64, _i32, _P,
+                                        _P, _P]),
     "mqs_free_batch": (C.c_int, [_P, _i32]),
     "mqs_free_mesh": (C.c_int, [_P, _i32]),
 }
@@ -216,6 +219,17 @@ def mqs_profile_read(ctx):
     out = np.zeros(5)
     _check("mqs_profile_read", load().mqs_profile_read(ctx, _ptr(out)))
     return out
+
+
+def mqs_propagate_noalloc(device, stream, n, rowptr, colidx, nnz, n_lanes, A, M, K, Dinv,
+                          n_phases, F, src_amp, src_phase, t0, dt, n_steps, freq_hz, qoi_kind,
+                          cg_tol, cg_max_iters, a_out, qoi_out, status_out=None):
+    """Sequential stepping that allocates no memory (see include/mqs.h);
+    array arguments are device tensors except src_amp/src_phase (host or device)."""
+    _check("mqs_propagate_noalloc", load().mqs_propagate_noalloc(
+        device, stream, n, _ptr(rowptr), _ptr(colidx), nnz, n_lanes, _ptr(A), _ptr(M), _ptr(K),
+        _ptr(Dinv), n_phases, _ptr(F), _ptr(src_amp), _ptr(src_phase), t0, dt, n_steps, freq_hz,
+        qoi_kind, cg_tol, cg_max_iters, _ptr(a_out), _ptr(qoi_out), _ptr(status_out)))
 
 
 def mqs_free_batch(ctx, batch):
