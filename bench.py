@@ -234,6 +234,8 @@ def run_ours(args, wl, rank, world, dist):
 
     def one_step(params_src, qoi_dst):
         b = mqs.mqs_set_samples(ctx.h, mesh_id, params_src)
+        if args.solver == "banded":
+            mqs.mqs_set_solver(ctx.h, b, mqs.MQS_SOLVER_BANDED)
         mqs.mqs_set_time(ctx.h, b, 0.0, wl["t_end"], 50.0, wl["qoi"])
         k = mqs.mqs_propagate(ctx.h, b, 0, wl["dt"], 0.0, wl["n_slices"], wl["cf"],
                               wl["n_slices"], wl["par_tol"], prec, wl["cg_tol"], 20000)
@@ -347,7 +349,8 @@ def run_ours(args, wl, rank, world, dist):
                    "samples": ns, "steps": wl["n_steps"], "dt": wl["dt"],
                    "slices": wl["n_slices"], "coarse_factor": wl["cf"],
                    "parareal_tol": wl["par_tol"], "cg_tol": wl["cg_tol"],
-                   "precision": args.precision, "parareal_iters": ks[-1],
+                   "precision": args.precision, "solver": args.solver,
+                   "parareal_iters": ks[-1],
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": statistics.median(times), "p99_ms": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
@@ -377,6 +380,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare"])
+    ap.add_argument("--solver", default="pcg", choices=["pcg", "banded"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -45,6 +45,10 @@ extern "C" {
 #define MQS_FP64   0      /* FP64 Jacobi-PCG */
 #define MQS_MIXED  1      /* FP32 matrix values and SpMV inside FP64 PCG, FP64 residual replacement */
 
+/* linear solver of the implicit-Euler systems (mqs_set_solver) */
+#define MQS_SOLVER_PCG    0  /* batched Jacobi-preconditioned CG (default) */
+#define MQS_SOLVER_BANDED 1  /* band Cholesky in reverse Cuthill-McKee order, FP64 */
+
 /* quantity of interest */
 #define MQS_QOI_ENERGY 0  /* (1/N) sum_{k=1..N} 1/2 a_k^T K a_k (time-averaged magnetic energy) */
 #define MQS_QOI_JOULE  1  /* (1/T) sum_k (a_{k+1}-a_k)^T M (a_{k+1}-a_k) / dt  (Eq. 26, mean joule loss) */
@@ -52,6 +56,7 @@ extern "C" {
 /* per-sample status bits returned by mqs_read_qoi */
 #define MQS_ST_NOTCONV 1  /* some step's linear solve stopped at the iteration limit */
 #define MQS_ST_NONFINITE 2 /* a residual norm became NaN or Inf */
+#define MQS_ST_NOTSPD  4  /* a band Cholesky factorisation met a non-positive pivot */
 
 typedef struct mqs_ctx mqs_ctx;
 
@@ -111,6 +116,18 @@ int mqs_set_samples(mqs_ctx* ctx, int32_t mesh_id, int32_t n_samples, int32_t n_
  * (MQS_QOI_*) of a batch.  Must be called before mqs_propagate. */
 int mqs_set_time(mqs_ctx* ctx, int32_t batch_id, double t0, double t_end,
                  double freq_hz, int32_t qoi_kind);
+
+/* Select the linear solver used by later mqs_propagate calls on a batch
+ * (MQS_SOLVER_PCG or MQS_SOLVER_BANDED).  Both solve Eq. 7's system
+ * (M/dt + K) a_{k+1} = b each step.  The banded solver factors M/dt + K once
+ * per sample and step size (band Cholesky after a reverse Cuthill-McKee
+ * ordering of the free unknowns, n x (bw+1) doubles per factor) and then does
+ * one forward and one backward substitution per step.  It has no iteration
+ * tolerance (cg_tol, cg_max_iters are ignored) and supports MQS_FP64 only. */
+int mqs_set_solver(mqs_ctx* ctx, int32_t batch_id, int32_t solver);
+
+/* Bandwidth of a mesh's reverse Cuthill-McKee ordering (used by the banded solver). */
+int mqs_mesh_bandwidth(mqs_ctx* ctx, int32_t mesh_id, int32_t* bandwidth);
 
 /* Run one MLMC level for every sample of the batch (Eq. 7, Eq. 9, Eq. 12):
  * the level-l solve with step dt_level and, if dt_prev > 0, the companion

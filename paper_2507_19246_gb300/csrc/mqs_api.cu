@@ -39,6 +39,26 @@ struct ValueSet {
   DevBuf A, A32, Dinv;
 };
 
+struct FactorSet {
+  double dt = 0.0;
+  DevBuf LB, invd, bad;   // [samples][n][bw+1], [samples][n], [samples]
+};
+
+// Lanes of the banded direct solver: one CTA per lane, vectors lane-major.
+struct DirectSet {
+  int lanes = 0, n = 0;
+  DevBuf vec, qraw, desc;
+  std::vector<DirectLane> host;
+  int ensure(int lanes_, int n_) {
+    lanes = lanes_;
+    n = n_;
+    MQS_TRY(vec.ensure((size_t)lanes * 4 * n * sizeof(double)));
+    MQS_TRY(qraw.ensure((size_t)lanes * sizeof(double)));
+    return MQS_OK;
+  }
+  double* v(int lane, int j) const { return vec.as<double>() + ((size_t)lane * 4 + j) * n; }
+};
+
 struct LaneSet {
   int lanes = 0;
   int64_t xs = 0;
@@ -87,6 +107,13 @@ struct Batch {
   DevBuf qoi, status;
   int level = 0;
   double stats[MQS_N_STATS] = {};
+  // banded direct solver
+  int solver = MQS_SOLVER_PCG;
+  std::vector<double> hparams;                 // host copy of the parameters
+  std::vector<std::unique_ptr<FactorSet>> fsets;
+  DirectSet dplain, dpar, dchain;
+  DevBuf E;                                    // Parareal fine ends, lane-major
+  int nf_direct = 0;
 };
 
 struct Ctx {
@@ -522,6 +549,202 @@ int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
   return MQS_OK;
 }
 
+
+FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, int& rc) {
+  rc = MQS_OK;
+  for (auto& f : b.fsets)
+    if (f->dt == dt) return f.get();
+  ValueSet* v = value_set(ctx, b, m, dt, false, rc);
+  if (!v) return nullptr;
+  b.fsets.emplace_back(new FactorSet());
+  FactorSet* f = b.fsets.back().get();
+  f->dt = dt;
+  const size_t fstride = (size_t)m.n_free * (m.bw + 1);
+  if ((rc = f->LB.ensure(fstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
+  if ((rc = f->invd.ensure((size_t)m.n_free * b.n * sizeof(double))) != MQS_OK) return nullptr;
+  if ((rc = f->bad.ensure((size_t)b.n * sizeof(int32_t))) != MQS_OK) return nullptr;
+  rc = band_factor(m, v->A.as<double>(), b.n, b.n, f->LB.as<double>(), f->invd.as<double>(),
+                   f->bad.as<int32_t>(), ctx->c.stream);
+  return rc == MQS_OK ? f : nullptr;
+}
+
+DirectConst direct_const(const MeshDev& m, const Batch& b) {
+  DirectConst kc;
+  memset(&kc, 0, sizeof(kc));
+  kc.rowptr = m.rowptr.as<int32_t>();
+  kc.colidx = m.colidx.as<int32_t>();
+  kc.iperm = m.iperm.as<int32_t>();
+  kc.M = b.Mv.as<double>();
+  kc.K = b.qoi_kind == MQS_QOI_ENERGY ? b.Kv.as<double>() : nullptr;
+  kc.vs = b.n;
+  kc.F = m.F.as<double>();
+  kc.n = m.n_free;
+  kc.bw = m.bw;
+  kc.n_phases = m.n_phases;
+  kc.qoi_kind = b.qoi_kind;
+  kc.omega = kTwoPi * b.freq;
+  return kc;
+}
+
+DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int sample,
+                       double* a0, double* a1, double* y, double* w, double* qoi_out,
+                       int n_steps, int64_t k0, int init_from_a0) {
+  DirectLane d;
+  memset(&d, 0, sizeof(d));
+  const size_t fstride = (size_t)m.n_free * (m.bw + 1);
+  d.LB = f.LB.as<double>() + fstride * sample;
+  d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
+  d.a0 = a0;
+  d.a1 = a1;
+  d.y = y;
+  d.w = w;
+  d.qoi_out = qoi_out;
+  d.vcol = sample;
+  const int R = m.n_regions, P = m.n_phases;
+  const double* p = b.hparams.data() + (size_t)sample * b.n_params;
+  for (int q = 0; q < kMaxPhases; ++q) {
+    d.amp[q] = q < P ? p[2 * R] * p[2 * R + 1 + q] : 0.0;
+    d.phase[q] = q < P ? p[2 * R + 1 + P + q] : 0.0;
+  }
+  d.dt = f.dt;
+  d.t0 = b.t0;
+  d.k0 = k0;
+  d.n_steps = n_steps;
+  d.init_from_a0 = init_from_a0;
+  d.sample = sample;
+  return d;
+}
+
+int upload_direct(mqs_ctx* ctx, DirectSet& ds) {
+  MQS_TRY(ds.desc.ensure(std::max<size_t>(1, ds.host.size()) * sizeof(DirectLane)));
+  if (!ds.host.empty())
+    MQS_CUDA_TRY(cudaMemcpyAsync(ds.desc.p, ds.host.data(), ds.host.size() * sizeof(DirectLane),
+                                 cudaMemcpyHostToDevice, ctx->c.stream));
+  return MQS_OK;
+}
+
+// Sequential stepping with the banded solver: lanes [0, nf) level l, [nf, nf+nc) level l-1.
+int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* ff, int nsf,
+                     const FactorSet* fc, int nsc) {
+  const int nf = ff ? b.n : 0, nc = fc ? b.n : 0;
+  DirectSet& ds = b.dplain;
+  MQS_TRY(ds.ensure(nf + nc, m.n_free));
+  MQS_CUDA_TRY(cudaMemsetAsync(ds.qraw.p, 0, (size_t)(nf + nc) * sizeof(double), ctx->c.stream));
+  ds.host.clear();
+  for (int s = 0; s < nf; ++s)
+    ds.host.push_back(direct_lane(m, b, *ff, s, ds.v(s, 0), ds.v(s, 1), ds.v(s, 2), ds.v(s, 3),
+                                  ds.qraw.as<double>() + s, nsf, 0, 0));
+  for (int s = 0; s < nc; ++s) {
+    const int l = nf + s;
+    ds.host.push_back(direct_lane(m, b, *fc, s, ds.v(l, 0), ds.v(l, 1), ds.v(l, 2), ds.v(l, 3),
+                                  ds.qraw.as<double>() + l, nsc, 0, 0));
+  }
+  b.nf_direct = nf;
+  MQS_TRY(upload_direct(ctx, ds));
+  const DirectConst kc = direct_const(m, b);
+  MQS_TRY(prof_mark(ctx->c, 0, true));
+  MQS_TRY(launch_direct(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
+  MQS_TRY(prof_mark(ctx->c, 0, false));
+  b.stats[1] += (double)nf * nsf + (double)nc * nsc;
+  b.stats[2] += (double)nf * nsf + (double)nc * nsc;
+  b.stats[6] += (double)nf * nsf + (double)nc * nsc;
+  return MQS_OK;
+}
+
+int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet& fF,
+                        const FactorSet& fC, int n_steps, int M, int cf, int max_iters, double tol,
+                        int& iters_out) {
+  const cudaStream_t st = ctx->c.stream;
+  const int S = n_steps / M, Sc = S / cf, ns = b.n, n = m.n_free;
+  const int lanes = ns * M;
+  const size_t field = (size_t)lanes * n * sizeof(double);
+  MQS_TRY(b.U.ensure(field));
+  MQS_TRY(b.G.ensure(field));
+  MQS_TRY(b.E.ensure(field));
+  MQS_TRY(b.jump2.ensure((size_t)lanes * sizeof(double)));
+  MQS_TRY(b.norm2.ensure((size_t)lanes * sizeof(double)));
+  MQS_TRY(b.dpar.ensure(lanes, n));
+  MQS_TRY(b.dchain.ensure(ns, n));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.U.p, 0, field, st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.G.p, 0, field, st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.norm2.p, 0, (size_t)lanes * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.qraw.p, 0, (size_t)lanes * sizeof(double), st));
+  const DirectConst kc = direct_const(m, b);
+  DirectSet& dc = b.dchain;
+  dc.host.clear();
+  for (int s = 0; s < ns; ++s)
+    dc.host.push_back(direct_lane(m, b, fC, s, dc.v(s, 0), dc.v(s, 1), dc.v(s, 2), dc.v(s, 3),
+                                  dc.qraw.as<double>() + s, Sc, 0, 1));
+  MQS_TRY(upload_direct(ctx, dc));
+  DirectChain ch;
+  ch.U = b.U.as<double>();
+  ch.E = b.E.as<double>();
+  ch.G = b.G.as<double>();
+  ch.M = M;
+  ch.steps_per_slice = Sc;
+  ch.jump2 = b.jump2.as<double>();
+  ch.norm2 = b.norm2.as<double>();
+  ch.s_begin = 0;
+  ch.first_sweep = 1;
+  MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
+  MQS_TRY(prof_mark(ctx->c, 1, true));
+  MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kc, ch, st));
+  MQS_TRY(prof_mark(ctx->c, 1, false));
+  double exec_steps = (double)ns * (M - 1) * Sc, chain_steps = exec_steps, fine_steps = 0.0;
+  std::vector<double> hj((size_t)lanes), hn((size_t)lanes);
+  DirectSet& dp = b.dpar;
+  int k = 0;
+  for (k = 1; k <= max_iters; ++k) {
+    MQS_CUDA_TRY(cudaMemcpyAsync(b.E.p, b.U.p, field, cudaMemcpyDeviceToDevice, st));
+    dp.host.clear();
+    for (int s = 0; s < ns; ++s)
+      for (int j = k - 1; j < M; ++j) {
+        const int l = s * M + j, c = (int)dp.host.size();
+        dp.host.push_back(direct_lane(m, b, fF, s, b.E.as<double>() + (size_t)l * n, dp.v(c, 1),
+                                      dp.v(c, 2), dp.v(c, 3), dp.qraw.as<double>() + l, S,
+                                      (int64_t)j * S, 1));
+      }
+    fine_steps += (double)dp.host.size() * S;
+    exec_steps += (double)dp.host.size() * S;
+    MQS_TRY(upload_direct(ctx, dp));
+    MQS_TRY(prof_mark(ctx->c, 0, true));
+    MQS_TRY(launch_direct(dp.desc.as<DirectLane>(), (int)dp.host.size(), kc, st));
+    MQS_TRY(prof_mark(ctx->c, 0, false));
+    MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
+    if (k - 1 <= M - 2) {
+      ch.s_begin = k - 1;
+      ch.first_sweep = 0;
+      MQS_TRY(prof_mark(ctx->c, 1, true));
+      MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kc, ch, st));
+      MQS_TRY(prof_mark(ctx->c, 1, false));
+      exec_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
+      chain_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
+    }
+    MQS_CUDA_TRY(cudaMemcpyAsync(hj.data(), b.jump2.p, hj.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    MQS_CUDA_TRY(cudaMemcpyAsync(hn.data(), b.norm2.p, hn.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    MQS_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int s = 0; s < ns; ++s) {
+      double num = 0.0, den = 0.0;
+      for (int j = 0; j < M; ++j) {
+        num = std::max(num, std::sqrt(hj[(size_t)s * M + j]));
+        den = std::max(den, std::sqrt(hn[(size_t)s * M + j]));
+      }
+      const double jump = den > 0.0 ? num / den : num;
+      if (!(jump <= tol)) all = false;
+    }
+    if (all || k >= M) break;
+  }
+  iters_out = std::min(k, max_iters);
+  b.stats[1] += exec_steps;
+  b.stats[2] += (double)ns * n_steps;
+  b.stats[6] += fine_steps;
+  b.stats[7] += chain_steps;
+  return MQS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -655,6 +878,18 @@ int mqs_upload_mesh(mqs_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_t
     colidx.insert(colidx.end(), v.begin(), v.end());
   }
   m.nnz = (int64_t)colidx.size();
+  // reverse Cuthill-McKee ordering and the lower-band position of each nonzero
+  std::vector<int32_t> perm, iperm(m.n_free), band_idx(m.nnz);
+  int32_t bw = 0;
+  rcm_order(m.n_free, rowptr, colidx, perm, bw);
+  for (int32_t i = 0; i < m.n_free; ++i) iperm[perm[i]] = i;
+  if ((int64_t)m.n_free * (bw + 1) >= (int64_t)INT32_MAX) bw = -1;   // too wide for the band solver
+  for (int32_t i = 0; i < m.n_free; ++i)
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int32_t pi = iperm[i], pj = iperm[colidx[k]];
+      band_idx[k] = (bw >= 0 && pj <= pi) ? pi * (bw + 1) + (pj - pi + bw) : -1;
+    }
+  m.bw = bw;
   // element contributions per nonzero, sorted by (nonzero, code)
   std::vector<std::pair<int32_t, int32_t>> kc;
   kc.reserve((size_t)n_tri * 9);
@@ -704,10 +939,39 @@ int mqs_upload_mesh(mqs_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_t
                                cudaMemcpyHostToDevice, st));
   MQS_CUDA_TRY(cudaMemcpyAsync(m.diag.p, diag.data(), diag.size() * sizeof(int32_t),
                                cudaMemcpyHostToDevice, st));
+  MQS_TRY(m.perm.ensure(perm.size() * sizeof(int32_t)));
+  MQS_TRY(m.iperm.ensure(iperm.size() * sizeof(int32_t)));
+  MQS_TRY(m.band_idx.ensure(band_idx.size() * sizeof(int32_t)));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.perm.p, perm.data(), perm.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.iperm.p, iperm.data(), iperm.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  MQS_CUDA_TRY(cudaMemcpyAsync(m.band_idx.p, band_idx.data(), band_idx.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
   MQS_TRY(assemble_region_matrices(m, xy, tri, region, src_phase, src_coef, cptr, contrib, lptr,
                                    load, st));
   ctx->c.meshes.push_back(std::move(mesh));
   *mesh_id = (int32_t)ctx->c.meshes.size() - 1;
+  return MQS_OK;
+}
+
+int mqs_set_solver(mqs_ctx* ctx, int32_t batch_id, int32_t solver) {
+  MQS_TRY(enter(ctx));
+  Batch* b = get_batch(ctx, batch_id);
+  if (!b) return MQS_EINVAL;
+  if (solver != MQS_SOLVER_PCG && solver != MQS_SOLVER_BANDED) {
+    set_error("unknown solver %d", solver);
+    return MQS_EINVAL;
+  }
+  b->solver = solver;
+  return MQS_OK;
+}
+
+int mqs_mesh_bandwidth(mqs_ctx* ctx, int32_t mesh_id, int32_t* bandwidth) {
+  MQS_TRY(enter(ctx));
+  MeshDev* m = get_mesh(ctx, mesh_id);
+  if (!m || !bandwidth) return MQS_EINVAL;
+  *bandwidth = m->bw;
   return MQS_OK;
 }
 
@@ -741,6 +1005,9 @@ int mqs_set_samples(mqs_ctx* ctx, int32_t mesh_id, int32_t n_samples, int32_t n_
   const size_t bytes = (size_t)n_samples * n_params * sizeof(double);
   MQS_TRY(b->params.ensure(bytes));
   MQS_CUDA_TRY(cudaMemcpyAsync(b->params.p, params, bytes, cudaMemcpyDefault, ctx->c.stream));
+  b->hparams.resize((size_t)n_samples * n_params);
+  MQS_CUDA_TRY(cudaMemcpyAsync(b->hparams.data(), b->params.p, bytes, cudaMemcpyDeviceToHost,
+                               ctx->c.stream));
   MQS_TRY(b->qoi.ensure((size_t)n_samples * 2 * sizeof(double)));
   MQS_TRY(b->status.ensure((size_t)n_samples * sizeof(int32_t)));
   MQS_CUDA_TRY(cudaMemsetAsync(b->qoi.p, 0, (size_t)n_samples * 2 * sizeof(double), ctx->c.stream));
@@ -805,6 +1072,44 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
   const bool mixed = precision == MQS_MIXED;
   MQS_TRY(ensure_mk(ctx, b, m));
   int rc = MQS_OK;
+  if (b.solver == MQS_SOLVER_BANDED) {
+    if (mixed || m.bw < 0) {
+      set_error("the banded solver supports MQS_FP64 only and needs n_free * (bw + 1) < 2^31");
+      return MQS_EINVAL;
+    }
+    FactorSet* ff = factor_set(ctx, b, m, dt_level, rc);
+    if (!ff) return rc;
+    FactorSet* fc = nullptr;
+    if (dt_prev > 0.0 && !(fc = factor_set(ctx, b, m, dt_prev, rc))) return rc;
+    b.level = level;
+    b.has_coarse = fc != nullptr;
+    for (double& x : b.stats) x = 0.0;
+    b.stats[3] = m.n_free;
+    int par_iters = 0;
+    const cudaStream_t st = ctx->c.stream;
+    if (n_slices == 1) {
+      MQS_TRY(run_plain_direct(ctx, b, m, ff, nsf, fc, nsc));
+      b.mode = 3;
+      b.M = 1;
+      MQS_TRY(finish_qoi(b.dplain.qraw.as<double>(),
+                         fc ? b.dplain.qraw.as<double>() + b.nf_direct : nullptr, b.n, 1,
+                         qoi_scale(b.qoi_kind, nsf, dt_level),
+                         fc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
+    } else {
+      if (fc) MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc));
+      FactorSet* fC = factor_set(ctx, b, m, dt_level * coarse_factor, rc);
+      if (!fC) return rc;
+      MQS_TRY(run_parareal_direct(ctx, b, m, *ff, *fC, nsf, n_slices, coarse_factor,
+                                  max_par_iters, par_tol, par_iters));
+      b.mode = 4;
+      b.M = n_slices;
+      MQS_TRY(finish_qoi(b.dpar.qraw.as<double>(), fc ? b.dplain.qraw.as<double>() : nullptr,
+                         b.n, n_slices, qoi_scale(b.qoi_kind, nsf, dt_level),
+                         fc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
+    }
+    if (par_iters_out) *par_iters_out = par_iters;
+    return MQS_OK;
+  }
   ValueSet* vf = value_set(ctx, b, m, dt_level, mixed, rc);
   if (!vf) return rc;
   ValueSet* vc = nullptr;
@@ -874,6 +1179,16 @@ int mqs_read_qoi(mqs_ctx* ctx, int32_t batch_id, double* qoi, int32_t* status) {
       MQS_TRY(fold(b->par, b->n * b->M, b->M, 0));
       MQS_TRY(fold(b->chain, b->n, 1, 0));
       if (b->has_coarse) MQS_TRY(fold(b->plain, b->n, 1, 0));
+    } else if (b->mode >= 3) {
+      // a non-positive pivot in any factor of the sample
+      std::vector<int32_t> h((size_t)b->n);
+      for (auto& f : b->fsets) {
+        MQS_CUDA_TRY(cudaMemcpyAsync(h.data(), f->bad.p, h.size() * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st));
+        MQS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int s2 = 0; s2 < b->n; ++s2)
+          if (h[s2]) out[s2] |= MQS_ST_NOTSPD;
+      }
     }
     MQS_CUDA_TRY(cudaMemcpyAsync(status, out.data(), out.size() * sizeof(int32_t),
                                  cudaMemcpyDefault, st));
@@ -899,7 +1214,20 @@ int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a) {
     MQS_TRY(tmp.ensure((size_t)b->n * m.n_free * sizeof(double)));
     out = tmp.as<double>();
   }
-  if (which == 0 && b->mode == 2) {
+  if (b->mode >= 3) {
+    const size_t row = (size_t)m.n_free * sizeof(double);
+    const double* src;
+    size_t pitch;
+    if (which == 0 && b->mode == 4) {
+      src = b->E.as<double>() + (size_t)(b->M - 1) * m.n_free;
+      pitch = row * b->M;
+    } else {
+      const int lane0 = which == 0 ? 0 : b->nf_direct;
+      src = b->dplain.v(lane0, 0);
+      pitch = row * 4;
+    }
+    MQS_CUDA_TRY(cudaMemcpy2DAsync(out, row, src, pitch, row, b->n, cudaMemcpyDeviceToDevice, st));
+  } else if (which == 0 && b->mode == 2) {
     MQS_TRY(transpose_to_rows(b->par.vec(V_A0), b->par.xs, m.n_free, b->n, b->M, b->M - 1, out, st));
   } else if (which == 0) {
     MQS_TRY(transpose_to_rows(b->plain.vec(V_A0), b->plain.xs, m.n_free, b->n, 1, 0, out, st));
@@ -923,7 +1251,9 @@ int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats) {
     return MQS_EINVAL;
   }
   double prop = 0.0, chain = 0.0, t;
-  if (b->mode == 1 || b->has_coarse) {
+  if (b->mode >= 3) {
+    // the banded solver has no iterations
+  } else if (b->mode == 1 || b->has_coarse) {
     MQS_TRY(sum_host(ctx, b->plain.iters, b->plain.xs, t));
     prop += t;
   }

@@ -1,0 +1,378 @@
+// Banded direct solver for the implicit-Euler systems (Sec. II-A, Eq. 7):
+// (M/dt + K) is factored once per (sample, dt) by a band Cholesky
+// decomposition in a reverse Cuthill-McKee ordering and every step does one
+// forward and one backward substitution.
+//
+// Layout.  A factor is stored by rows: row i holds L(i, i-bw .. i) at
+// LB[i*(bw+1) + (c - i + bw)] (entries left of column 0 stay zero), plus the
+// reciprocal diagonal invd[i] = 1 / L(i, i).  Lane vectors of this solver are
+// lane-major ([lane][n]) because one CTA advances one lane.
+//
+// Kernels.
+//  * k_band_fill   scatters the lower-band entries of each sample's A values.
+//  * k_band_chol   right-looking band Cholesky, one CTA per factor, in place:
+//                  for each column j, L_jj = sqrt(A_jj), scale the column,
+//                  rank-1 update of the bw x bw trailing triangle.
+//  * k_direct_propagate  one CTA per lane walks all time steps: right-hand
+//                  side (original order) scattered into the permuted work
+//                  vector, blocked forward and backward substitution (32-row
+//                  blocks: a CTA-wide GEMV against the solved part, then a
+//                  warp-level triangular solve of the 32 x 32 diagonal block),
+//                  gather back, QoI and y = M a.
+//  * k_direct_chain  the Parareal coarse sweep (one CTA per sample) with the
+//                  Eq. 12 correction and jump norms fused, lane-major state.
+#include "mqs_internal.cuh"
+
+#include <algorithm>
+
+namespace mqs {
+namespace {
+
+constexpr int kDT = 512;          // threads per CTA
+constexpr int kDW = kDT / 32;     // warps per CTA
+constexpr int kBlk = 32;          // substitution block (rows)
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA-wide sum (warp butterfly, then warps in order).
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int j = 0; j < kDW; ++j) s += red[j];
+  return s;
+}
+
+__global__ void k_band_fill(int64_t nnz, const int32_t* __restrict__ band_idx,
+                            const double* __restrict__ A, int64_t vs, int n_fac,
+                            int64_t fstride, double* __restrict__ LB) {
+  const int64_t total = nnz * n_fac;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / n_fac;
+    const int f = (int)(t % n_fac);
+    const int32_t b = band_idx[k];
+    if (b >= 0) LB[f * fstride + b] = A[k * vs + f];
+  }
+}
+
+__global__ void __launch_bounds__(kDT) k_band_chol(double* __restrict__ LBall,
+                                                  double* __restrict__ invd_all, int n, int bw,
+                                                  int64_t fstride, int32_t* __restrict__ bad) {
+  extern __shared__ double colj[];   // bw entries of the current column
+  __shared__ double s_inv;
+  double* LB = LBall + blockIdx.x * fstride;
+  double* invd = invd_all + (int64_t)blockIdx.x * n;
+  const int W = bw + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = LB[(int64_t)j * W + bw];
+      if (!(d > 0.0)) {   // not positive definite: record and continue on a unit pivot
+        bad[blockIdx.x] = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      LB[(int64_t)j * W + bw] = d;
+      s_inv = 1.0 / d;
+      invd[j] = s_inv;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int t = threadIdx.x; t < bw; t += kDT) {
+      const int i = j + 1 + t;
+      double v = 0.0;
+      if (i < n) {
+        const int64_t o = (int64_t)i * W + (j - i + bw);
+        v = LB[o] * inv;
+        LB[o] = v;
+      }
+      colj[t] = v;
+    }
+    __syncthreads();
+    // A(i, k) -= L(i, j) L(k, j) for j < k <= i <= j + bw
+    for (int a = warp; a < bw; a += kDW) {
+      const int i = j + 1 + a;
+      if (i >= n) break;
+      const double ca = colj[a];
+      if (ca == 0.0) continue;
+      double* row = LB + (int64_t)i * W + (j + 1 - i + bw);   // column j+1 of row i
+      for (int b = lane; b <= a; b += 32) row[b] = fma(-ca, colj[b], row[b]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- substitution
+struct SolveSmem {
+  double sacc[kBlk];
+  double diag[kBlk][kBlk + 1];
+  double part[kDW][kBlk];
+  double red[kDW];
+};
+
+// L z = w in place (w permuted), blocked.
+__device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ invd,
+                              int n, int bw, double* w, SolveSmem& sm) {
+  const int W = bw + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < n; i0 += kBlk) {
+    // rows of the block against the already solved columns [i - bw, i0)
+    for (int r = warp; r < kBlk; r += kDW) {
+      const int i = i0 + r;
+      double acc = 0.0;
+      if (i < n) {
+        const int jlo = max(0, i - bw);
+        const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L(i, c)
+        for (int c = jlo + lane; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) sm.sacc[r] = i < n ? w[i] - acc : 0.0;
+    }
+    // diagonal block, lower triangle
+    for (int t = threadIdx.x; t < kBlk * kBlk; t += kDT) {
+      const int r = t / kBlk, c = t % kBlk;
+      const int i = i0 + r, cc = i0 + c;
+      sm.diag[r][c] = (c < r && i < n && r - c <= bw) ? LB[(int64_t)i * W + (cc - i + bw)] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int i = i0 + lane;
+      const bool ok = i < n;
+      double v = sm.sacc[lane];
+      const double inv = ok ? invd[i] : 0.0;
+      double mine = 0.0;
+      const int jm = min(kBlk, n - i0);
+      for (int j = 0; j < jm; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, v * inv, j);
+        if (lane == j) mine = yj;
+        if (lane > j) v = fma(-sm.diag[lane][j], yj, v);
+      }
+      if (ok) w[i] = mine;
+    }
+    __syncthreads();
+  }
+}
+
+// L^T x = z in place, blocked, from the last block up.
+__device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ invd,
+                               int n, int bw, double* w, SolveSmem& sm) {
+  const int W = bw + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int last = ((n - 1) / kBlk) * kBlk;
+  for (int i0 = last; i0 >= 0; i0 -= kBlk) {
+    // contributions of the solved rows k >= i0 + kBlk: x_col -= L(k, col) x_k
+    const int col = i0 + lane;
+    double acc = 0.0;
+    const int kend = min(n - 1, i0 + kBlk - 1 + bw);
+    for (int k = i0 + kBlk + warp; k <= kend; k += kDW) {
+      const int off = col - k + bw;
+      if (col < n && off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
+    }
+    sm.part[warp][lane] = acc;
+    for (int t = threadIdx.x; t < kBlk * kBlk; t += kDT) {
+      const int r = t / kBlk, c = t % kBlk;       // diag[r][c] = L(i0 + r, i0 + c), c < r
+      const int i = i0 + r, cc = i0 + c;
+      sm.diag[r][c] = (c < r && i < n && r - c <= bw) ? LB[(int64_t)i * W + (cc - i + bw)] : 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int i = i0 + lane;
+      const bool ok = i < n;
+      double s = 0.0;
+      for (int q = 0; q < kDW; ++q) s += sm.part[q][lane];
+      double v = ok ? w[i] - s : 0.0;
+      const double inv = ok ? invd[i] : 0.0;
+      double mine = 0.0;
+      const int jm = min(kBlk, n - i0);
+      for (int j = jm - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(0xffffffffu, v * inv, j);
+        if (lane == j) mine = xj;
+        if (lane < j) v = fma(-sm.diag[j][lane], xj, v);
+      }
+      if (ok) w[i] = mine;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr,
+                                          const int32_t* __restrict__ colidx, int i,
+                                          const double* __restrict__ vals, int64_t vs,
+                                          const double* x) {
+  double acc = 0.0;
+  for (int k = __ldg(rowptr + i); k < __ldg(rowptr + i + 1); ++k)
+    acc = fma(__ldg(vals + (int64_t)k * vs), x[__ldg(colidx + k)], acc);
+  return acc;
+}
+
+struct DLaneOut {
+  double qoi;
+};
+
+// Advance one lane by n_steps implicit-Euler steps with the direct solver.
+// On return the final state is in a0 (as given).
+__device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int n_steps,
+                                 int64_t k0, SolveSmem& sm, DLaneOut& out) {
+  const int n = kc.n;
+  double* a0 = D.a0;
+  double* a1 = D.a1;
+  double* y = D.y;
+  double* w = D.w;
+  const double* Mv = kc.M + D.vcol;
+  const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
+  if (D.init_from_a0) {
+    for (int i = threadIdx.x; i < n; i += kDT) y[i] = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a0);
+  } else {
+    for (int i = threadIdx.x; i < n; i += kDT) {
+      a0[i] = 0.0;
+      y[i] = 0.0;
+    }
+  }
+  __syncthreads();
+  double qacc = 0.0;
+  const double dt = D.dt;
+  for (int step = 0; step < n_steps; ++step) {
+    const double t = D.t0 + (double)(k0 + step + 1) * dt;
+    double g[kMaxPhases];
+#pragma unroll
+    for (int ph = 0; ph < kMaxPhases; ++ph) {
+      g[ph] = 0.0;
+      if (ph < kc.n_phases) {
+        const double arg = kc.omega * t - (2.0 * kPi * ph) / kc.n_phases + D.phase[ph];
+        g[ph] = D.amp[ph] * sin(arg);
+      }
+    }
+    for (int i = threadIdx.x; i < n; i += kDT) {
+      double f = 0.0;
+#pragma unroll
+      for (int ph = 0; ph < kMaxPhases; ++ph)
+        if (ph < kc.n_phases) f = fma(g[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
+      w[__ldg(kc.iperm + i)] = y[i] / dt + f;
+    }
+    __syncthreads();
+    forward_subst(D.LB, D.invd, n, kc.bw, w, sm);
+    backward_subst(D.LB, D.invd, n, kc.bw, w, sm);
+    for (int i = threadIdx.x; i < n; i += kDT) a1[i] = w[__ldg(kc.iperm + i)];
+    __syncthreads();
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += kDT) {
+      const double yn = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a1);
+      if (kc.qoi_kind == MQS_QOI_JOULE) {
+        part = fma(a1[i] - a0[i], yn - y[i], part);
+      } else {
+        part = fma(a1[i], csr_row(kc.rowptr, kc.colidx, i, Kv, kc.vs, a1), part);
+      }
+      y[i] = yn;
+    }
+    const double red = block_sum(part, sm.red);
+    qacc += kc.qoi_kind == MQS_QOI_JOULE ? red / dt : 0.5 * red;
+    double* tmp = a0;
+    a0 = a1;
+    a1 = tmp;
+    __syncthreads();
+  }
+  if (n_steps & 1) {
+    for (int i = threadIdx.x; i < n; i += kDT) a1[i] = a0[i];
+    __syncthreads();
+  }
+  out.qoi = qacc;
+}
+
+__global__ void __launch_bounds__(kDT) k_direct_propagate(const DirectLane* __restrict__ lanes,
+                                                         DirectConst kc) {
+  __shared__ SolveSmem sm;
+  const DirectLane D = lanes[blockIdx.x];
+  DLaneOut out;
+  direct_integrate(kc, D, D.n_steps, D.k0, sm, out);
+  if (threadIdx.x == 0) D.qoi_out[0] = out.qoi;
+}
+
+// Parareal coarse sweep, one CTA per sample; slice states lane-major
+// U/E/G[(sample*M + s) * n + i].
+__global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restrict__ lanes,
+                                                     DirectConst kc, DirectChain ch) {
+  __shared__ SolveSmem sm;
+  DirectLane D = lanes[blockIdx.x];
+  const int n = kc.n;
+  const int sample = D.sample;
+  D.init_from_a0 = 1;
+  for (int s = ch.s_begin; s < ch.M - 1; ++s) {
+    const int64_t base = ((int64_t)sample * ch.M + s) * n;
+    for (int i = threadIdx.x; i < n; i += kDT) D.a0[i] = ch.U[base + i];
+    __syncthreads();
+    DLaneOut out;
+    direct_integrate(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
+    double j2 = 0.0, u2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += kDT) {
+      const double gn = D.a0[i];
+      const double un = ch.first_sweep ? gn : ch.E[base + i] + (gn - ch.G[base + i]);
+      const double du = un - ch.U[base + n + i];
+      j2 = fma(du, du, j2);
+      u2 = fma(un, un, u2);
+      ch.U[base + n + i] = un;
+      ch.G[base + i] = gn;
+    }
+    j2 = block_sum(j2, sm.red);
+    u2 = block_sum(u2, sm.red);
+    if (threadIdx.x == 0) {
+      ch.jump2[(int64_t)sample * ch.M + s + 1] = j2;
+      ch.norm2[(int64_t)sample * ch.M + s + 1] = u2;
+    }
+    __syncthreads();
+  }
+}
+
+int grid_of(int64_t total, int block) {
+  int64_t g = (total + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 1 << 20));
+}
+
+}  // namespace
+
+int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
+                double* invd, int32_t* bad, cudaStream_t st) {
+  const int bw = m.bw;
+  const int64_t fstride = (int64_t)m.n_free * (bw + 1);
+  MQS_CUDA_TRY(cudaMemsetAsync(LB, 0, (size_t)fstride * n_fac * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(bad, 0, (size_t)n_fac * sizeof(int32_t), st));
+  k_band_fill<<<grid_of(m.nnz * n_fac, 256), 256, 0, st>>>(m.nnz, m.band_idx.as<int32_t>(), A, vs,
+                                                         n_fac, fstride, LB);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  const size_t smem = (size_t)std::max(bw, 1) * sizeof(double);
+  if (smem > 48 * 1024)
+    MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  k_band_chol<<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return MQS_OK;
+}
+
+int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  k_direct_propagate<<<n_lanes, kDT, 0, st>>>(d_lanes, kc);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return MQS_OK;
+}
+
+int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                        const DirectChain& ch, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  k_direct_chain<<<n_lanes, kDT, 0, st>>>(d_lanes, kc, ch);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return MQS_OK;
+}
+
+}  // namespace mqs

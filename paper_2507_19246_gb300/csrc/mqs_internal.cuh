@@ -78,7 +78,15 @@ struct MeshDev {
   DevBuf F;                      // [P][n_free] per-phase load vectors (double)
   std::vector<int32_t> free_node;
   int live_batches = 0;
+  // banded direct solver: reverse Cuthill-McKee ordering of the free unknowns
+  int32_t bw = -1;               // lower bandwidth in the new ordering (-1: not built)
+  DevBuf perm, iperm;            // perm[new] = old, iperm[old] = new (int32)
+  DevBuf band_idx;               // [nnz] position of a lower-band entry in [n][bw+1], -1 above
 };
+
+// Reverse Cuthill-McKee ordering of a symmetric CSR pattern (host).
+void rcm_order(int n, const std::vector<int32_t>& rowptr, const std::vector<int32_t>& colidx,
+               std::vector<int32_t>& perm, int32_t& bandwidth);
 
 // ---------------------------------------------------------------- solve lanes
 // One tile = L consecutive lanes that share a step size and a step count and
@@ -144,6 +152,44 @@ struct ChainDesc {
 
 // process-wide count of kernels launched by the library
 void count_launch(int n = 1);
+
+// ---------------------------------------------------------------- banded direct solver
+struct DirectLane {
+  const double* LB;        // this lane's band Cholesky factor [n][bw+1]
+  const double* invd;      // its reciprocal diagonal [n]
+  double *a0, *a1, *y, *w; // lane vectors [n] (lane-major)
+  double* qoi_out;         // raw QoI sum of the run
+  int64_t vcol;            // value column (sample) of M / K values
+  double amp[kMaxPhases], phase[kMaxPhases];
+  double dt, t0;
+  int64_t k0;              // global index of the first step
+  int32_t n_steps, init_from_a0, sample, pad_;
+};
+
+struct DirectConst {
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const int32_t* iperm;    // original -> band ordering
+  const double* M;         // [nnz][vs] sample values
+  const double* K;
+  int64_t vs;
+  const double* F;         // [P][n]
+  int32_t n, bw, n_phases, qoi_kind;
+  double omega;
+};
+
+struct DirectChain {
+  double *U, *E, *G;       // [samples][M][n] slice starts, fine ends, previous coarse ends
+  int32_t M, s_begin, steps_per_slice, first_sweep;
+  double *jump2, *norm2;   // [samples][M]
+};
+
+// mqs_direct.cu
+int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
+                double* invd, int32_t* bad, cudaStream_t st);
+int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
+int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                        const DirectChain& ch, cudaStream_t st);
 
 // launchers (mqs_team.cu)
 int launch_propagate(const TileDesc* d_tiles, int n_tiles, int L, int C, int precision,

@@ -21,7 +21,8 @@ from . import build as _build
 MQS_OK, MQS_EINVAL, MQS_ENOMEM, MQS_ECUDA, MQS_ENOTCONV = 0, -1, -2, -3, -4
 MQS_FP64, MQS_MIXED = 0, 1
 MQS_QOI_ENERGY, MQS_QOI_JOULE = 0, 1
-MQS_ST_NOTCONV, MQS_ST_NONFINITE = 1, 2
+MQS_ST_NOTCONV, MQS_ST_NONFINITE, MQS_ST_NOTSPD = 1, 2, 4
+MQS_SOLVER_PCG, MQS_SOLVER_BANDED = 0, 1
 
 _lib = None
 _P = C.c_void_p
@@ -35,6 +36,8 @@ _SIGS = {
     "mqs_upload_mesh": (C.c_int, [_P, _i32, _P, _i32, _P, _P, _i32, _P, _P, _P, _i32,
                                   C.POINTER(_i32)]),
     "mqs_mesh_info": (C.c_int, [_P, _i32, C.POINTER(_i32), C.POINTER(_i64)]),
+    "mqs_mesh_bandwidth": (C.c_int, [_P, _i32, C.POINTER(_i32)]),
+    "mqs_set_solver": (C.c_int, [_P, _i32, _i32]),
     "mqs_set_samples": (C.c_int, [_P, _i32, _i32, _i32, _P, C.POINTER(_i32)]),
     "mqs_set_time": (C.c_int, [_P, _i32, _f64, _f64, _f64, _i32]),
     "mqs_propagate": (C.c_int, [_P, _i32, _i32, _f64, _f64, _i32, _i32, _i32, _f64, _i32, _f64,
@@ -149,6 +152,16 @@ def mqs_mesh_info(ctx, mesh_id):
     n, z = _i32(), _i64()
     _check("mqs_mesh_info", load().mqs_mesh_info(ctx, mesh_id, C.byref(n), C.byref(z)))
     return n.value, z.value
+
+
+def mqs_mesh_bandwidth(ctx, mesh_id) -> int:
+    bw = _i32()
+    _check("mqs_mesh_bandwidth", load().mqs_mesh_bandwidth(ctx, mesh_id, C.byref(bw)))
+    return bw.value
+
+
+def mqs_set_solver(ctx, batch, solver):
+    _check("mqs_set_solver", load().mqs_set_solver(ctx, batch, solver))
 
 
 def mqs_set_samples(ctx, mesh_id, params) -> int:
@@ -274,6 +287,12 @@ class Context:
 
     def mesh_info(self, mesh_id):
         return mqs_mesh_info(self.h, mesh_id)
+
+    def mesh_bandwidth(self, mesh_id):
+        return mqs_mesh_bandwidth(self.h, mesh_id)
+
+    def set_solver(self, batch, solver):
+        mqs_set_solver(self.h, batch, solver)
 
     def set_samples(self, mesh_id, params) -> int:
         b = mqs_set_samples(self.h, mesh_id, params)

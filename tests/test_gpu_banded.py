@@ -1,0 +1,130 @@
+"""The banded direct solver (band Cholesky in RCM order) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import fem, parareal, stepper
+from workloads import configs, meshes, params
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mqs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2507_19246_gb300 import mqs as m
+    m.load()
+    return m
+
+
+@pytest.fixture()
+def ctx(mqs):
+    c = mqs.Context(0)
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+def test_bandwidth_is_reported(ctx):
+    for name, lim in (("5k", 60), ("20k", 230)):
+        mid = ctx.upload_mesh(meshes.annulus(name))
+        bw = ctx.mesh_bandwidth(mid)
+        assert 0 < bw <= lim
+
+
+def test_banded_square_energy_full_config(ctx, mqs):
+    cfg = configs.MC_SQUARE
+    mesh = meshes.unit_square(16)
+    p = params.square_samples(cfg.n_samples)
+    dt = cfg.t_end / cfg.n_steps
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, cfg.t_end, 50.0, mqs.MQS_QOI_ENERGY)
+    ctx.propagate(b, 0, dt)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    for s in range(cfg.n_samples):
+        qo, ao, _ = stepper.solve_sample(mesh, p[s], dt, cfg.n_steps, stepper.QOI_ENERGY)
+        assert abs(q[s, 0] - qo) <= TOL * abs(qo) and _rel(a[s], ao) <= TOL
+
+
+def test_banded_level_pair_ragged_annulus(ctx, mqs):
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(37, 1)
+    dt1, dt0 = configs.level_dt(1), configs.level_dt(0)
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, configs.PERIOD, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 1, dt1, dt_prev=dt0)
+    q, st = ctx.read_qoi(b)
+    a, ac = ctx.read_state(b, 0), ctx.read_state(b, 1)
+    assert not st.any()
+    for s in range(p.shape[0]):
+        qf, af, _ = stepper.solve_sample(mesh, p[s], dt1, 128, stepper.QOI_JOULE)
+        qc, acc, _ = stepper.solve_sample(mesh, p[s], dt0, 64, stepper.QOI_JOULE)
+        assert abs(q[s, 0] - qf) <= TOL * abs(qf) and abs(q[s, 1] - qc) <= TOL * abs(qc), s
+        assert _rel(a[s], af) <= TOL and _rel(ac[s], acc) <= TOL, s
+
+
+def test_banded_parareal_matches_oracle_parareal(ctx, mqs):
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(2, 0, seed=8)
+    n_steps, M, cf, tol = 256, 16, 4, 1e-8
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+    K = ctx.propagate(b, 0, dt, n_slices=M, coarse_factor=cf, max_par_iters=M, par_tol=tol)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    Ks = []
+    for s in range(2):
+        d = fem.Discretisation(mesh, p[s])
+        ref = parareal.parareal_sample(d, dt, n_steps, M, cf, tol, stepper.QOI_JOULE)
+        Ks.append(ref["iters"])
+        if ref["iters"] == K:
+            q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
+            assert abs(q[s, 0] - q_ref) <= TOL * abs(q_ref)
+            assert _rel(a[s], ref["a_end"]) <= TOL
+    assert K == max(Ks)          # the batch iterates until every sample converged
+
+
+def test_banded_parareal_K_equals_M_is_serial(ctx, mqs):
+    mesh = meshes.annulus("5k")
+    p = params.annulus_nominal(1)
+    n_steps, M, cf = 64, 8, 2
+    dt = configs.PERIOD / 64
+    mid = ctx.upload_mesh(mesh)
+    q, a = [], []
+    for slices in (M, 1):
+        b = ctx.set_samples(mid, p)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+        ctx.propagate(b, 0, dt, n_slices=slices, coarse_factor=cf, max_par_iters=slices,
+                      par_tol=0.0)
+        q.append(ctx.read_qoi(b)[0][0, 0])
+        a.append(ctx.read_state(b, 0)[0])
+    # same kernel, same factor, same per-lane arithmetic: the state is exact, as in
+    # the oracle; the QoI differs only by the order of the per-slice partial sums
+    assert np.array_equal(a[0], a[1])
+    assert q[0] == pytest.approx(q[1], rel=1e-14)
+
+
+def test_banded_rejects_mixed_precision(ctx, mqs):
+    mesh = meshes.unit_square(8)
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, params.square_samples(2))
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 0.02, 50.0, mqs.MQS_QOI_JOULE)
+    with pytest.raises(mqs.MQSError, match="FP64"):
+        ctx.propagate(b, 0, 0.02 / 16, precision=mqs.MQS_MIXED)
