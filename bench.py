@@ -148,6 +148,14 @@ def algorithmic_flops(n_free, nnz, lane_iters, lane_steps):
     return n_free * (lane_iters * (2 * zn + 13) + lane_steps * (4 * zn + 8))
 
 
+def banded_flops(n_free, nnz, bw, lane_steps):
+    """Algorithmic FP64 flops of banded-solver stepping: per lane-step the
+    forward and backward substitutions (sum over rows of min(i, bw) FMAs each,
+    ~ n bw - bw^2/2) plus the right-hand side and the QoI / y = M a SpMV."""
+    subst = 2 * 2 * (n_free * bw - bw * bw / 2.0)
+    return lane_steps * (subst + n_free * (2.0 * nnz / n_free + 10.0))
+
+
 # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -308,8 +316,13 @@ def run_ours(args, wl, rank, world, dist):
     dominant = "stepping" if step_ms >= sweep_ms else "coarse_sweep"
     d_ms, d_n, d_bytes = (step_ms, step_n, step_bytes) if dominant == "stepping" else \
         (sweep_ms, sweep_n, sweep_bytes)
-    d_flops = sum(algorithmic_flops(n_free, nnz, s[4], s[6]) if dominant == "stepping" else
-                  algorithmic_flops(n_free, nnz, s[5], s[7]) for s in stats)
+    if args.solver == "banded":
+        bw = mqs.mqs_mesh_bandwidth(ctx.h, mesh_id)
+        d_flops = sum(banded_flops(n_free, nnz, bw, s[6] if dominant == "stepping" else s[7])
+                      for s in stats)
+    else:
+        d_flops = sum(algorithmic_flops(n_free, nnz, s[4], s[6]) if dominant == "stepping" else
+                      algorithmic_flops(n_free, nnz, s[5], s[7]) for s in stats)
     hbm_gbs = (d_bytes / max(d_n, 1)) / (d_ms / max(d_n, 1) / 1e3) / 1e9 if d_ms > 0 else 0.0
     if args.precision == "fp64":
         # the FP64 Jacobi-PCG works out of L2 and is bound by the FP64 pipe

@@ -583,6 +583,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b) {
   kc.n_phases = m.n_phases;
   kc.qoi_kind = b.qoi_kind;
   kc.omega = kTwoPi * b.freq;
+  kc.w_in_smem = m.n_free <= direct_smem_max_n() ? 1 : 0;
   return kc;
 }
 

@@ -132,7 +132,17 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
       if (i < n) {
         const int jlo = max(0, i - bw);
         const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L(i, c)
-        for (int c = jlo + lane; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = jlo + lane;
+        for (; c + 96 < i0; c += 128) {
+          const double l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
+          acc = fma(l0, w[c], acc);
+          a1 = fma(l1, w[c + 32], a1);
+          a2 = fma(l2, w[c + 64], a2);
+          a3 = fma(l3, w[c + 96], a3);
+        }
+        for (; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
+        acc = (acc + a1) + (a2 + a3);
       }
       acc = warp_sum(acc);
       if (lane == 0) sm.sacc[r] = i < n ? w[i] - acc : 0.0;
@@ -171,13 +181,24 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
   for (int i0 = last; i0 >= 0; i0 -= kBlk) {
     // contributions of the solved rows k >= i0 + kBlk: x_col -= L(k, col) x_k
     const int col = i0 + lane;
-    double acc = 0.0;
+    double acc = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     const int kend = min(n - 1, i0 + kBlk - 1 + bw);
-    for (int k = i0 + kBlk + warp; k <= kend; k += kDW) {
+    int k = i0 + kBlk + warp;
+    // rows k with k - col <= bw for every lane of the block need no test
+    for (; k + 3 * kDW <= kend && k + 3 * kDW - i0 <= bw; k += 4 * kDW) {
+      const double* r0 = LB + (int64_t)k * W + (col - k + bw);
+      const double l0 = r0[0], l1 = r0[kDW * (W - 1)], l2 = r0[2 * kDW * (W - 1)],
+                   l3 = r0[3 * kDW * (W - 1)];
+      acc = fma(l0, w[k], acc);
+      a1 = fma(l1, w[k + kDW], a1);
+      a2 = fma(l2, w[k + 2 * kDW], a2);
+      a3 = fma(l3, w[k + 3 * kDW], a3);
+    }
+    for (; k <= kend; k += kDW) {
       const int off = col - k + bw;
       if (col < n && off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
     }
-    sm.part[warp][lane] = acc;
+    sm.part[warp][lane] = (acc + a1) + (a2 + a3);
     for (int t = threadIdx.x; t < kBlk * kBlk; t += kDT) {
       const int r = t / kBlk, c = t % kBlk;       // diag[r][c] = L(i0 + r, i0 + c), c < r
       const int i = i0 + r, cc = i0 + c;
@@ -226,7 +247,8 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
   double* a0 = D.a0;
   double* a1 = D.a1;
   double* y = D.y;
-  double* w = D.w;
+  extern __shared__ double w_smem[];
+  double* w = kc.w_in_smem ? w_smem : D.w;
   const double* Mv = kc.M + D.vcol;
   const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
   if (D.init_from_a0) {
@@ -331,6 +353,14 @@ __global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restri
   }
 }
 
+}  // namespace
+
+// Largest n whose work vector fits next to the static shared memory of the
+// stepping kernels (227 KB per CTA on sm_103).
+int direct_smem_max_n() { return (int)((227 * 1024 - (int)sizeof(SolveSmem) - 1024) / sizeof(double)); }
+
+namespace {
+
 int grid_of(int64_t total, int block) {
   int64_t g = (total + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 1 << 20));
@@ -358,9 +388,17 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double
   return MQS_OK;
 }
 
+size_t direct_smem(const DirectConst& kc) {
+  return kc.w_in_smem ? (size_t)kc.n * sizeof(double) : 0;
+}
+
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  k_direct_propagate<<<n_lanes, kDT, 0, st>>>(d_lanes, kc);
+  const size_t smem = direct_smem(kc);
+  if (smem > 48 * 1024)
+    MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_direct_propagate<<<n_lanes, kDT, smem, st>>>(d_lanes, kc);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
@@ -369,7 +407,11 @@ int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  k_direct_chain<<<n_lanes, kDT, 0, st>>>(d_lanes, kc, ch);
+  const size_t smem = direct_smem(kc);
+  if (smem > 48 * 1024)
+    MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  k_direct_chain<<<n_lanes, kDT, smem, st>>>(d_lanes, kc, ch);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

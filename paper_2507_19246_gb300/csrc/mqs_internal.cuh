@@ -176,6 +176,8 @@ struct DirectConst {
   const double* F;         // [P][n]
   int32_t n, bw, n_phases, qoi_kind;
   double omega;
+  int32_t w_in_smem;       // 1: the permuted work vector lives in shared memory
+  int32_t pad_;
 };
 
 struct DirectChain {
@@ -188,6 +190,7 @@ struct DirectChain {
 int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
                 double* invd, int32_t* bad, cudaStream_t st);
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
+int direct_smem_max_n();
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st);
 
