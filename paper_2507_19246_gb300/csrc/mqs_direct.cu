@@ -379,9 +379,8 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   const size_t smem = (size_t)std::max(bw, 1) * sizeof(double);
-  if (smem > 48 * 1024)
-    MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
   k_band_chol<<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
@@ -394,10 +393,9 @@ size_t direct_smem(const DirectConst& kc) {
 
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  const size_t smem = direct_smem(kc);
-  if (smem > 48 * 1024)
-    MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = direct_smem(kc);   // on top of the static SolveSmem
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_direct_propagate<<<n_lanes, kDT, smem, st>>>(d_lanes, kc);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
@@ -408,9 +406,8 @@ int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectCons
                         const DirectChain& ch, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
   const size_t smem = direct_smem(kc);
-  if (smem > 48 * 1024)
-    MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
   k_direct_chain<<<n_lanes, kDT, smem, st>>>(d_lanes, kc, ch);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
