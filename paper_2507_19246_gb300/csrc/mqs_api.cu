@@ -41,7 +41,7 @@ struct ValueSet {
 
 struct FactorSet {
   double dt = 0.0;
-  DevBuf LB, invd, bad;   // [samples][n][bw+1], [samples][n], [samples]
+  DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
 };
 
 // Lanes of the banded direct solver: one CTA per lane, vectors lane-major.
@@ -563,8 +563,10 @@ FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, int& 
   if ((rc = f->LB.ensure(fstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
   if ((rc = f->invd.ensure((size_t)m.n_free * b.n * sizeof(double))) != MQS_OK) return nullptr;
   if ((rc = f->bad.ensure((size_t)b.n * sizeof(int32_t))) != MQS_OK) return nullptr;
+  const size_t bstride = (size_t)block_count(m.n_free) * 32 * 32;
+  if ((rc = f->Binv.ensure(bstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
   rc = band_factor(m, v->A.as<double>(), b.n, b.n, f->LB.as<double>(), f->invd.as<double>(),
-                   f->bad.as<int32_t>(), ctx->c.stream);
+                   f->Binv.as<double>(), f->bad.as<int32_t>(), ctx->c.stream);
   return rc == MQS_OK ? f : nullptr;
 }
 
@@ -595,6 +597,7 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   const size_t fstride = (size_t)m.n_free * (m.bw + 1);
   d.LB = f.LB.as<double>() + fstride * sample;
   d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
+  d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
   d.a0 = a0;
   d.a1 = a1;
   d.y = y;

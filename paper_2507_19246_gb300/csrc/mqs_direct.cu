@@ -4,8 +4,10 @@
 // forward and one backward substitution.
 //
 // Layout.  A factor is stored by rows: row i holds L(i, i-bw .. i) at
-// LB[i*(bw+1) + (c - i + bw)] (entries left of column 0 stay zero), plus the
-// reciprocal diagonal invd[i] = 1 / L(i, i).  Lane vectors of this solver are
+// LB[i*(bw+1) + (c - i + bw)] (entries left of column 0 stay zero); after the
+// factorisation every row is scaled to unit diagonal (L~ = D^-1 L), the
+// reciprocal diagonal invd[i] = 1 / L(i, i) is kept, and the inverse of each
+// 32 x 32 diagonal block of L~ is stored in Binv.  Lane vectors of this solver are
 // lane-major ([lane][n]) because one CTA advances one lane.
 //
 // Kernels.
@@ -111,115 +113,140 @@ __global__ void __launch_bounds__(kDT) k_band_chol(double* __restrict__ LBall,
   }
 }
 
+// ---------------------------------------------------------------- unit scaling
+// After factoring, each row is scaled by its reciprocal diagonal, L~ = D^-1 L
+// (unit diagonal), so that L y = b becomes L~ y = D^-1 b and L^T x = y becomes
+// L~^T u = y with x = D^-1 u.  The inverse of every 32 x 32 diagonal block of
+// L~ is stored as well, which turns the sequential in-block substitution into
+// a small dense product.
+__global__ void k_band_unit(double* __restrict__ LBall, const double* __restrict__ invd_all,
+                            int n, int bw, int64_t fstride, int n_fac) {
+  const int W = bw + 1;
+  const int64_t total = (int64_t)n * n_fac;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; t < total;
+       t += (int64_t)gridDim.x * blockDim.y) {
+    const int f = (int)(t / n), i = (int)(t % n);
+    double* row = LBall + f * fstride + (int64_t)i * W;
+    const double s = invd_all[(int64_t)f * n + i];
+    for (int d = threadIdx.x; d < bw; d += blockDim.x) row[d] *= s;
+    if (threadIdx.x == 0) row[bw] = 1.0;
+  }
+}
+
+// One warp per diagonal block: lane c solves L~_blk x = e_c (rows past n are identity).
+__global__ void k_block_inv(const double* __restrict__ LBall, double* __restrict__ Binv_all,
+                            int n, int bw, int64_t fstride, int nblk, int n_fac) {
+  __shared__ double xs[4][kBlk][kBlk + 1];
+  const int wl = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t g = blockIdx.x * 4LL + wl;
+  if (g >= (int64_t)nblk * n_fac) return;
+  const int f = (int)(g / nblk), blk = (int)(g % nblk);
+  const double* LB = LBall + f * fstride;
+  double* B = Binv_all + ((int64_t)f * nblk + blk) * kBlk * kBlk;
+  const int i0 = blk * kBlk, W = bw + 1;
+  for (int r = 0; r < kBlk; ++r) {
+    double x = (r == c) ? 1.0 : 0.0;
+    const int i = i0 + r;
+    if (i < n) {
+      for (int j = 0; j < r; ++j)
+        if (r - j <= bw) x = fma(-LB[(int64_t)i * W + (i0 + j - i + bw)], xs[wl][j][c], x);
+    }
+    xs[wl][r][c] = x;
+    __syncwarp();
+  }
+  for (int r = 0; r < kBlk; ++r) B[r * kBlk + c] = xs[wl][r][c];
+}
+
 // ---------------------------------------------------------------- substitution
 struct SolveSmem {
   double sacc[kBlk];
-  double diag[kBlk][kBlk + 1];
-  double part[kDW][kBlk];
+  double part[kBlk][kBlk + 1];   // forward: [row][lane]; backward: [warp][col]
   double red[kDW];
 };
 
-// L z = w in place (w permuted), blocked.
-__device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ invd,
+// L~ y = w in place (w already scaled by D^-1, permuted order), blocked.
+__device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                               int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 < n; i0 += kBlk) {
-    // rows of the block against the already solved columns [i - bw, i0)
+  for (int i0 = 0, blk = 0; i0 < n; i0 += kBlk, ++blk) {
+    // partial dot products of the block rows with the solved columns [i - bw, i0)
     for (int r = warp; r < kBlk; r += kDW) {
       const int i = i0 + r;
       double acc = 0.0;
       if (i < n) {
-        const int jlo = max(0, i - bw);
-        const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L(i, c)
-        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int c = jlo + lane;
+        const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L~(i, c)
+        int c = max(0, i - bw) + lane;
         for (; c + 96 < i0; c += 128) {
           const double l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
-          acc = fma(l0, w[c], acc);
-          a1 = fma(l1, w[c + 32], a1);
-          a2 = fma(l2, w[c + 64], a2);
-          a3 = fma(l3, w[c + 96], a3);
+          const double w0 = w[c], w1 = w[c + 32], w2 = w[c + 64], w3 = w[c + 96];
+          acc = fma(l0, w0, acc);
+          acc = fma(l1, w1, acc);
+          acc = fma(l2, w2, acc);
+          acc = fma(l3, w3, acc);
         }
         for (; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
-        acc = (acc + a1) + (a2 + a3);
       }
-      acc = warp_sum(acc);
-      if (lane == 0) sm.sacc[r] = i < n ? w[i] - acc : 0.0;
-    }
-    // diagonal block, lower triangle
-    for (int t = threadIdx.x; t < kBlk * kBlk; t += kDT) {
-      const int r = t / kBlk, c = t % kBlk;
-      const int i = i0 + r, cc = i0 + c;
-      sm.diag[r][c] = (c < r && i < n && r - c <= bw) ? LB[(int64_t)i * W + (cc - i + bw)] : 0.0;
+      sm.part[r][lane] = acc;
     }
     __syncthreads();
     if (warp == 0) {
       const int i = i0 + lane;
-      const bool ok = i < n;
-      double v = sm.sacc[lane];
-      const double inv = ok ? invd[i] : 0.0;
-      double mine = 0.0;
-      const int jm = min(kBlk, n - i0);
-      for (int j = 0; j < jm; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, v * inv, j);
-        if (lane == j) mine = yj;
-        if (lane > j) v = fma(-sm.diag[lane][j], yj, v);
-      }
-      if (ok) w[i] = mine;
+      double s = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) s += sm.part[lane][q];
+      sm.sacc[lane] = i < n ? w[i] - s : 0.0;
+      __syncwarp();
+      const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane * kBlk;   // row `lane`
+      double y = 0.0;
+      for (int c = 0; c <= lane; ++c) y = fma(B[c], sm.sacc[c], y);
+      if (i < n) w[i] = y;
     }
     __syncthreads();
   }
 }
 
-// L^T x = z in place, blocked, from the last block up.
-__device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ invd,
+// L~^T u = w in place, blocked, from the last block up.
+__device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                                int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int last = ((n - 1) / kBlk) * kBlk;
-  for (int i0 = last; i0 >= 0; i0 -= kBlk) {
-    // contributions of the solved rows k >= i0 + kBlk: x_col -= L(k, col) x_k
+  const int nblk = (n + kBlk - 1) / kBlk;
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int i0 = blk * kBlk;
+    // contributions of the solved rows k >= i0 + kBlk: u_col -= L~(k, col) u_k
     const int col = i0 + lane;
-    double acc = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double acc = 0.0;
     const int kend = min(n - 1, i0 + kBlk - 1 + bw);
     int k = i0 + kBlk + warp;
-    // rows k with k - col <= bw for every lane of the block need no test
     for (; k + 3 * kDW <= kend && k + 3 * kDW - i0 <= bw; k += 4 * kDW) {
       const double* r0 = LB + (int64_t)k * W + (col - k + bw);
       const double l0 = r0[0], l1 = r0[kDW * (W - 1)], l2 = r0[2 * kDW * (W - 1)],
                    l3 = r0[3 * kDW * (W - 1)];
-      acc = fma(l0, w[k], acc);
-      a1 = fma(l1, w[k + kDW], a1);
-      a2 = fma(l2, w[k + 2 * kDW], a2);
-      a3 = fma(l3, w[k + 3 * kDW], a3);
+      const double w0 = w[k], w1 = w[k + kDW], w2 = w[k + 2 * kDW], w3 = w[k + 3 * kDW];
+      acc = fma(l0, w0, acc);
+      acc = fma(l1, w1, acc);
+      acc = fma(l2, w2, acc);
+      acc = fma(l3, w3, acc);
     }
     for (; k <= kend; k += kDW) {
       const int off = col - k + bw;
       if (col < n && off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
     }
-    sm.part[warp][lane] = (acc + a1) + (a2 + a3);
-    for (int t = threadIdx.x; t < kBlk * kBlk; t += kDT) {
-      const int r = t / kBlk, c = t % kBlk;       // diag[r][c] = L(i0 + r, i0 + c), c < r
-      const int i = i0 + r, cc = i0 + c;
-      sm.diag[r][c] = (c < r && i < n && r - c <= bw) ? LB[(int64_t)i * W + (cc - i + bw)] : 0.0;
-    }
+    sm.part[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
       const int i = i0 + lane;
-      const bool ok = i < n;
       double s = 0.0;
+#pragma unroll
       for (int q = 0; q < kDW; ++q) s += sm.part[q][lane];
-      double v = ok ? w[i] - s : 0.0;
-      const double inv = ok ? invd[i] : 0.0;
-      double mine = 0.0;
-      const int jm = min(kBlk, n - i0);
-      for (int j = jm - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(0xffffffffu, v * inv, j);
-        if (lane == j) mine = xj;
-        if (lane < j) v = fma(-sm.diag[j][lane], xj, v);
-      }
-      if (ok) w[i] = mine;
+      sm.sacc[lane] = i < n ? w[i] - s : 0.0;
+      __syncwarp();
+      // u = (L~_blk^T)^-1 acc = (L~_blk^-1)^T acc: column `lane` of Binv
+      const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane;
+      double u = 0.0;
+      for (int c = lane; c < kBlk; ++c) u = fma(B[c * kBlk], sm.sacc[c], u);
+      if (i < n) w[i] = u;
     }
     __syncthreads();
   }
@@ -278,12 +305,16 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
 #pragma unroll
       for (int ph = 0; ph < kMaxPhases; ++ph)
         if (ph < kc.n_phases) f = fma(g[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
-      w[__ldg(kc.iperm + i)] = y[i] / dt + f;
+      const int pi = __ldg(kc.iperm + i);
+      w[pi] = (y[i] / dt + f) * D.invd[pi];          // D^-1 b
     }
     __syncthreads();
-    forward_subst(D.LB, D.invd, n, kc.bw, w, sm);
-    backward_subst(D.LB, D.invd, n, kc.bw, w, sm);
-    for (int i = threadIdx.x; i < n; i += kDT) a1[i] = w[__ldg(kc.iperm + i)];
+    forward_subst(D.LB, D.Binv, n, kc.bw, w, sm);
+    backward_subst(D.LB, D.Binv, n, kc.bw, w, sm);
+    for (int i = threadIdx.x; i < n; i += kDT) {
+      const int pi = __ldg(kc.iperm + i);
+      a1[i] = w[pi] * D.invd[pi];                     // x = D^-1 u
+    }
     __syncthreads();
     double part = 0.0;
     for (int i = threadIdx.x; i < n; i += kDT) {
@@ -355,6 +386,8 @@ __global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restri
 
 }  // namespace
 
+int block_count(int n) { return (n + kBlk - 1) / kBlk; }
+
 // Largest n whose work vector fits next to the static shared memory of the
 // stepping kernels (227 KB per CTA on sm_103).
 int direct_smem_max_n() { return (int)((227 * 1024 - (int)sizeof(SolveSmem) - 1024) / sizeof(double)); }
@@ -369,7 +402,7 @@ int grid_of(int64_t total, int block) {
 }  // namespace
 
 int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
-                double* invd, int32_t* bad, cudaStream_t st) {
+                double* invd, double* Binv, int32_t* bad, cudaStream_t st) {
   const int bw = m.bw;
   const int64_t fstride = (int64_t)m.n_free * (bw + 1);
   MQS_CUDA_TRY(cudaMemsetAsync(LB, 0, (size_t)fstride * n_fac * sizeof(double), st));
@@ -382,6 +415,15 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double
   MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   k_band_chol<<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  k_band_unit<<<grid_of((int64_t)m.n_free * n_fac, 8), dim3(32, 8), 0, st>>>(LB, invd, m.n_free, bw,
+                                                                          fstride, n_fac);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  const int nblk = (m.n_free + kBlk - 1) / kBlk;
+  k_block_inv<<<(unsigned)(((int64_t)nblk * n_fac + 3) / 4), 128, 0, st>>>(LB, Binv, m.n_free, bw,
+                                                                         fstride, nblk, n_fac);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

@@ -157,6 +157,7 @@ void count_launch(int n = 1);
 struct DirectLane {
   const double* LB;        // this lane's band Cholesky factor [n][bw+1]
   const double* invd;      // its reciprocal diagonal [n]
+  const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
   double *a0, *a1, *y, *w; // lane vectors [n] (lane-major)
   double* qoi_out;         // raw QoI sum of the run
   int64_t vcol;            // value column (sample) of M / K values
@@ -188,7 +189,8 @@ struct DirectChain {
 
 // mqs_direct.cu
 int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
-                double* invd, int32_t* bad, cudaStream_t st);
+                double* invd, double* Binv, int32_t* bad, cudaStream_t st);
+int block_count(int n);
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
 int direct_smem_max_n();
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
