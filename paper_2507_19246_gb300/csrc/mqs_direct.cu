@@ -30,10 +30,11 @@
 namespace mqs {
 namespace {
 
-constexpr int kDT = 512;          // threads per CTA
+constexpr int kDT = 1024;         // threads per CTA
 constexpr int kDW = kDT / 32;     // warps per CTA
 constexpr int kBlk = 32;          // substitution block (rows)
 constexpr double kPi = 3.14159265358979323846;
+static_assert(kDW == kBlk, "the partial-sum table is kBlk x kBlk");
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void k_block_inv(const double* __restrict__ LBall, double* __restrict
 // ---------------------------------------------------------------- substitution
 struct SolveSmem {
   double sacc[kBlk];
-  double part[kBlk][kBlk + 1];   // forward: [row][lane]; backward: [warp][col]
+  double part[kBlk][kBlk + 1];   // forward: [row][lane]; backward: [warp][col] (kDW == kBlk)
   double red[kDW];
 };
 
@@ -192,15 +193,27 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
     __syncthreads();
     if (warp == 0) {
       const int i = i0 + lane;
-      double s = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) s += sm.part[lane][q];
-      sm.sacc[lane] = i < n ? w[i] - s : 0.0;
+      // four independent partial chains keep the FP64 latency off the critical path
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        s0 += sm.part[lane][q];
+        s1 += sm.part[lane][q + 1];
+        s2 += sm.part[lane][q + 2];
+        s3 += sm.part[lane][q + 3];
+      }
+      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
       __syncwarp();
       const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane * kBlk;   // row `lane`
-      double y = 0.0;
-      for (int c = 0; c <= lane; ++c) y = fma(B[c], sm.sacc[c], y);
-      if (i < n) w[i] = y;
+      double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+#pragma unroll
+      for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
+        y0 = fma(B[c], sm.sacc[c], y0);
+        y1 = fma(B[c + 1], sm.sacc[c + 1], y1);
+        y2 = fma(B[c + 2], sm.sacc[c + 2], y2);
+        y3 = fma(B[c + 3], sm.sacc[c + 3], y3);
+      }
+      if (i < n) w[i] = (y0 + y1) + (y2 + y3);
     }
     __syncthreads();
   }
@@ -237,16 +250,27 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
     __syncthreads();
     if (warp == 0) {
       const int i = i0 + lane;
-      double s = 0.0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-      for (int q = 0; q < kDW; ++q) s += sm.part[q][lane];
-      sm.sacc[lane] = i < n ? w[i] - s : 0.0;
+      for (int q = 0; q < kDW; q += 4) {
+        s0 += sm.part[q][lane];
+        s1 += sm.part[q + 1][lane];
+        s2 += sm.part[q + 2][lane];
+        s3 += sm.part[q + 3][lane];
+      }
+      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
       __syncwarp();
       // u = (L~_blk^T)^-1 acc = (L~_blk^-1)^T acc: column `lane` of Binv
       const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane;
-      double u = 0.0;
-      for (int c = lane; c < kBlk; ++c) u = fma(B[c * kBlk], sm.sacc[c], u);
-      if (i < n) w[i] = u;
+      double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+#pragma unroll
+      for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
+        u0 = fma(B[c * kBlk], sm.sacc[c], u0);
+        u1 = fma(B[(c + 1) * kBlk], sm.sacc[c + 1], u1);
+        u2 = fma(B[(c + 2) * kBlk], sm.sacc[c + 2], u2);
+        u3 = fma(B[(c + 3) * kBlk], sm.sacc[c + 3], u3);
+      }
+      if (i < n) w[i] = (u0 + u1) + (u2 + u3);
     }
     __syncthreads();
   }
