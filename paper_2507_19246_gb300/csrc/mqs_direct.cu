@@ -34,7 +34,7 @@ constexpr int kDT = 1024;         // threads per CTA
 constexpr int kDW = kDT / 32;     // warps per CTA
 constexpr int kBlk = 32;          // substitution block (rows)
 constexpr double kPi = 3.14159265358979323846;
-static_assert(kDW == kBlk, "the partial-sum table is kBlk x kBlk");
+static_assert(kDW == kBlk, "the partial-sum tables are kBlk x kBlk");
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -159,52 +159,58 @@ __global__ void k_block_inv(const double* __restrict__ LBall, double* __restrict
 }
 
 // ---------------------------------------------------------------- substitution
+// Software-pipelined blocked substitution.  While the triangle warp (warp
+// kTri) finishes block b -- the coupling to the previous block, the
+// reduction of the partial sums and the product with the inverted diagonal
+// block -- the other warps compute the partial sums of block b+1 against all
+// columns solved before block b and stage the 32 x 32 coupling between blocks
+// b+1 and b into shared memory.
+constexpr int kTri = kDW - 1;
+constexpr int kGemvWarps = kDW - 1;
+
 struct SolveSmem {
+  double part[2][kBlk][kBlk + 1];   // [buffer][row][lane] partial sums
+  double off[2][kBlk][kBlk + 1];    // [buffer][row][col] coupling block
   double sacc[kBlk];
-  double part[kBlk][kBlk + 1];   // forward: [row][lane]; backward: [warp][col] (kDW == kBlk)
   double red[kDW];
 };
 
-// L~ y = w in place (w already scaled by D^-1, permuted order), blocked.
+// L~ y = w in place (w already scaled by D^-1, permuted order).
 __device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                               int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i0 = 0, blk = 0; i0 < n; i0 += kBlk, ++blk) {
-    // partial dot products of the block rows with the solved columns [i - bw, i0)
-    for (int r = warp; r < kBlk; r += kDW) {
-      const int i = i0 + r;
-      double acc = 0.0;
-      if (i < n) {
-        const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L~(i, c)
-        int c = max(0, i - bw) + lane;
-        for (; c + 96 < i0; c += 128) {
-          const double l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
-          const double w0 = w[c], w1 = w[c + 32], w2 = w[c + 64], w3 = w[c + 96];
-          acc = fma(l0, w0, acc);
-          acc = fma(l1, w1, acc);
-          acc = fma(l2, w2, acc);
-          acc = fma(l3, w3, acc);
-        }
-        for (; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
-      }
-      sm.part[r][lane] = acc;
-    }
-    __syncthreads();
-    if (warp == 0) {
+  const int nblk = (n + kBlk - 1) / kBlk;
+  // block 0 has no solved columns: empty partial sums and coupling
+  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += kDT) {
+    (&sm.part[0][0][0])[t] = 0.0;
+    (&sm.off[0][0][0])[t] = 0.0;
+  }
+  __syncthreads();
+  for (int b = 0; b < nblk; ++b) {
+    const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
+    if (warp == kTri) {
       const int i = i0 + lane;
-      // four independent partial chains keep the FP64 latency off the critical path
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {
-        s0 += sm.part[lane][q];
-        s1 += sm.part[lane][q + 1];
-        s2 += sm.part[lane][q + 2];
-        s3 += sm.part[lane][q + 3];
+        s0 += sm.part[cur][lane][q];
+        s1 += sm.part[cur][lane][q + 1];
+        s2 += sm.part[cur][lane][q + 2];
+        s3 += sm.part[cur][lane][q + 3];
+      }
+      if (b > 0) {   // coupling to block b-1 (solved in the previous round)
+#pragma unroll
+        for (int c = 0; c < kBlk; c += 4) {
+          s0 = fma(sm.off[cur][lane][c], w[i0 - kBlk + c], s0);
+          s1 = fma(sm.off[cur][lane][c + 1], w[i0 - kBlk + c + 1], s1);
+          s2 = fma(sm.off[cur][lane][c + 2], w[i0 - kBlk + c + 2], s2);
+          s3 = fma(sm.off[cur][lane][c + 3], w[i0 - kBlk + c + 3], s3);
+        }
       }
       sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
       __syncwarp();
-      const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane * kBlk;   // row `lane`
+      const double* B = Binv + (int64_t)b * kBlk * kBlk + lane * kBlk;   // row `lane`
       double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
 #pragma unroll
       for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
@@ -214,54 +220,73 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
         y3 = fma(B[c + 3], sm.sacc[c + 3], y3);
       }
       if (i < n) w[i] = (y0 + y1) + (y2 + y3);
+    } else if (b + 1 < nblk) {
+      // block b+1 against the columns solved before block b: [i - bw, i0)
+      const int j0 = i0 + kBlk;
+      for (int r = warp; r < kBlk; r += kGemvWarps) {
+        const int i = j0 + r;
+        double acc = 0.0;
+        if (i < n) {
+          const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L~(i, c)
+          int c = max(0, i - bw) + lane;
+          for (; c + 96 < i0; c += 128) {
+            const double l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
+            const double w0 = w[c], w1 = w[c + 32], w2 = w[c + 64], w3 = w[c + 96];
+            acc = fma(l0, w0, acc);
+            acc = fma(l1, w1, acc);
+            acc = fma(l2, w2, acc);
+            acc = fma(l3, w3, acc);
+          }
+          for (; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
+          // coupling L~(i, i0 + lane) to block b, inside the band
+          const int col = i0 + lane;
+          sm.off[nxt][r][lane] = (i - col <= bw) ? Lr[col] : 0.0;
+        } else {
+          sm.off[nxt][r][lane] = 0.0;
+        }
+        sm.part[nxt][r][lane] = acc;
+      }
     }
     __syncthreads();
   }
 }
 
-// L~^T u = w in place, blocked, from the last block up.
+// L~^T u = w in place, from the last block up.
 __device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                                int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kBlk - 1) / kBlk;
-  for (int blk = nblk - 1; blk >= 0; --blk) {
-    const int i0 = blk * kBlk;
-    // contributions of the solved rows k >= i0 + kBlk: u_col -= L~(k, col) u_k
-    const int col = i0 + lane;
-    double acc = 0.0;
-    const int kend = min(n - 1, i0 + kBlk - 1 + bw);
-    int k = i0 + kBlk + warp;
-    for (; k + 3 * kDW <= kend && k + 3 * kDW - i0 <= bw; k += 4 * kDW) {
-      const double* r0 = LB + (int64_t)k * W + (col - k + bw);
-      const double l0 = r0[0], l1 = r0[kDW * (W - 1)], l2 = r0[2 * kDW * (W - 1)],
-                   l3 = r0[3 * kDW * (W - 1)];
-      const double w0 = w[k], w1 = w[k + kDW], w2 = w[k + 2 * kDW], w3 = w[k + 3 * kDW];
-      acc = fma(l0, w0, acc);
-      acc = fma(l1, w1, acc);
-      acc = fma(l2, w2, acc);
-      acc = fma(l3, w3, acc);
-    }
-    for (; k <= kend; k += kDW) {
-      const int off = col - k + bw;
-      if (col < n && off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
-    }
-    sm.part[warp][lane] = acc;
-    __syncthreads();
-    if (warp == 0) {
+  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += kDT) {
+    (&sm.part[(nblk - 1) & 1][0][0])[t] = 0.0;
+    (&sm.off[(nblk - 1) & 1][0][0])[t] = 0.0;
+  }
+  __syncthreads();
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
+    if (warp == kTri) {
       const int i = i0 + lane;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-      for (int q = 0; q < kDW; q += 4) {
-        s0 += sm.part[q][lane];
-        s1 += sm.part[q + 1][lane];
-        s2 += sm.part[q + 2][lane];
-        s3 += sm.part[q + 3][lane];
+      for (int q = 0; q < 32; q += 4) {        // part[cur][q][col]: q = GEMV slot
+        s0 += sm.part[cur][q][lane];
+        s1 += sm.part[cur][q + 1][lane];
+        s2 += sm.part[cur][q + 2][lane];
+        s3 += sm.part[cur][q + 3][lane];
+      }
+      if (b + 1 < nblk) {   // coupling to block b+1: rows i0+32+c, column i0+lane
+#pragma unroll
+        for (int c = 0; c < kBlk; c += 4) {
+          s0 = fma(sm.off[cur][c][lane], w[i0 + kBlk + c], s0);
+          s1 = fma(sm.off[cur][c + 1][lane], w[i0 + kBlk + c + 1], s1);
+          s2 = fma(sm.off[cur][c + 2][lane], w[i0 + kBlk + c + 2], s2);
+          s3 = fma(sm.off[cur][c + 3][lane], w[i0 + kBlk + c + 3], s3);
+        }
       }
       sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
       __syncwarp();
-      // u = (L~_blk^T)^-1 acc = (L~_blk^-1)^T acc: column `lane` of Binv
-      const double* B = Binv + (int64_t)blk * kBlk * kBlk + lane;
+      // u = (L~_blk^-1)^T acc: column `lane` of the inverted block
+      const double* B = Binv + (int64_t)b * kBlk * kBlk + lane;
       double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
 #pragma unroll
       for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
@@ -271,6 +296,36 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
         u3 = fma(B[(c + 3) * kBlk], sm.sacc[c + 3], u3);
       }
       if (i < n) w[i] = (u0 + u1) + (u2 + u3);
+    } else if (b > 0) {
+      // block b-1 (columns j0 .. j0+31) against the rows solved before block b:
+      // k in [i0 + 32, j0 + 31 + bw]
+      const int j0 = i0 - kBlk;
+      const int col = j0 + lane;
+      double acc = 0.0;
+      const int kend = min(n - 1, j0 + kBlk - 1 + bw);
+      int k = i0 + kBlk + warp;
+      for (; k + 3 * kGemvWarps <= kend && k + 3 * kGemvWarps - j0 <= bw; k += 4 * kGemvWarps) {
+        const double* r0 = LB + (int64_t)k * W + (col - k + bw);
+        const double l0 = r0[0], l1 = r0[kGemvWarps * (W - 1)], l2 = r0[2 * kGemvWarps * (W - 1)],
+                     l3 = r0[3 * kGemvWarps * (W - 1)];
+        const double w0 = w[k], w1 = w[k + kGemvWarps], w2 = w[k + 2 * kGemvWarps],
+                     w3 = w[k + 3 * kGemvWarps];
+        acc = fma(l0, w0, acc);
+        acc = fma(l1, w1, acc);
+        acc = fma(l2, w2, acc);
+        acc = fma(l3, w3, acc);
+      }
+      for (; k <= kend; k += kGemvWarps) {
+        const int off = col - k + bw;
+        if (off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
+      }
+      sm.part[nxt][warp][lane] = acc;
+      if (warp == 0) sm.part[nxt][kBlk - 1][lane] = 0.0;   // slot of the triangle warp
+      // coupling rows i0 + r (block b) x column j0 + lane (block b-1)
+      for (int r = warp; r < kBlk; r += kGemvWarps) {
+        const int kk = i0 + r;
+        sm.off[nxt][r][lane] = (kk < n && kk - col <= bw) ? LB[(int64_t)kk * W + (col - kk + bw)] : 0.0;
+      }
     }
     __syncthreads();
   }
