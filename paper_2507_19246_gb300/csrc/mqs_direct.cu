@@ -274,13 +274,15 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
         s2 += sm.part[cur][q + 2][lane];
         s3 += sm.part[cur][q + 3][lane];
       }
-      if (b + 1 < nblk) {   // coupling to block b+1: rows i0+32+c, column i0+lane
+      if (b + 1 < nblk) {   // coupling to block b+1: rows i0+32+c (< n), column i0+lane
+        const int kb = i0 + kBlk;
+        const int cm = min(kBlk, n - kb);                 // rows of block b+1 that exist
 #pragma unroll
         for (int c = 0; c < kBlk; c += 4) {
-          s0 = fma(sm.off[cur][c][lane], w[i0 + kBlk + c], s0);
-          s1 = fma(sm.off[cur][c + 1][lane], w[i0 + kBlk + c + 1], s1);
-          s2 = fma(sm.off[cur][c + 2][lane], w[i0 + kBlk + c + 2], s2);
-          s3 = fma(sm.off[cur][c + 3][lane], w[i0 + kBlk + c + 3], s3);
+          if (c < cm) s0 = fma(sm.off[cur][c][lane], w[kb + c], s0);
+          if (c + 1 < cm) s1 = fma(sm.off[cur][c + 1][lane], w[kb + c + 1], s1);
+          if (c + 2 < cm) s2 = fma(sm.off[cur][c + 2][lane], w[kb + c + 2], s2);
+          if (c + 3 < cm) s3 = fma(sm.off[cur][c + 3][lane], w[kb + c + 3], s3);
         }
       }
       sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
