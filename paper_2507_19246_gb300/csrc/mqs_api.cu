@@ -570,7 +570,9 @@ FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, int& 
   return rc == MQS_OK ? f : nullptr;
 }
 
-DirectConst direct_const(const MeshDev& m, const Batch& b) {
+// lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
+// vector in L2, several per SM (env MQS_DIRECT_WIDE=1/0 forces a choice).
+DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm) {
   DirectConst kc;
   memset(&kc, 0, sizeof(kc));
   kc.rowptr = m.rowptr.as<int32_t>();
@@ -585,7 +587,9 @@ DirectConst direct_const(const MeshDev& m, const Batch& b) {
   kc.n_phases = m.n_phases;
   kc.qoi_kind = b.qoi_kind;
   kc.omega = kTwoPi * b.freq;
-  kc.w_in_smem = m.n_free <= direct_smem_max_n() ? 1 : 0;
+  const int forced = env_int("MQS_DIRECT_WIDE", -1);
+  const bool wide = forced >= 0 ? forced == 1 : lanes < 2 * n_sm;
+  kc.w_in_smem = (wide && m.n_free <= direct_smem_max_n()) ? 1 : 0;
   return kc;
 }
 
@@ -645,7 +649,7 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* 
   }
   b.nf_direct = nf;
   MQS_TRY(upload_direct(ctx, ds));
-  const DirectConst kc = direct_const(m, b);
+  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm);
   MQS_TRY(prof_mark(ctx->c, 0, true));
   MQS_TRY(launch_direct(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
   MQS_TRY(prof_mark(ctx->c, 0, false));
@@ -673,7 +677,8 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
   MQS_CUDA_TRY(cudaMemsetAsync(b.G.p, 0, field, st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.norm2.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.qraw.p, 0, (size_t)lanes * sizeof(double), st));
-  const DirectConst kc = direct_const(m, b);
+  const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm);
+  const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm);
   DirectSet& dc = b.dchain;
   dc.host.clear();
   for (int s = 0; s < ns; ++s)
@@ -692,7 +697,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
   ch.first_sweep = 1;
   MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_TRY(prof_mark(ctx->c, 1, true));
-  MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kc, ch, st));
+  MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kchain, ch, st));
   MQS_TRY(prof_mark(ctx->c, 1, false));
   double exec_steps = (double)ns * (M - 1) * Sc, chain_steps = exec_steps, fine_steps = 0.0;
   std::vector<double> hj((size_t)lanes), hn((size_t)lanes);
@@ -719,7 +724,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
       ch.s_begin = k - 1;
       ch.first_sweep = 0;
       MQS_TRY(prof_mark(ctx->c, 1, true));
-      MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kc, ch, st));
+      MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kchain, ch, st));
       MQS_TRY(prof_mark(ctx->c, 1, false));
       exec_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
       chain_steps += (double)ns * (M - 1 - (k - 1)) * Sc;

@@ -34,7 +34,6 @@ constexpr int kDT = 1024;         // threads per CTA
 constexpr int kDW = kDT / 32;     // warps per CTA
 constexpr int kBlk = 32;          // substitution block (rows)
 constexpr double kPi = 3.14159265358979323846;
-static_assert(kDW == kBlk, "the partial-sum tables are kBlk x kBlk");
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -43,6 +42,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Deterministic CTA-wide sum (warp butterfly, then warps in order).
+template <int NT>
 __device__ double block_sum(double v, double* red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -50,7 +50,7 @@ __device__ double block_sum(double v, double* red) {
   if (l == 0) red[w] = v;
   __syncthreads();
   double s = 0.0;
-  for (int j = 0; j < kDW; ++j) s += red[j];
+  for (int j = 0; j < NT / 32; ++j) s += red[j];
   return s;
 }
 
@@ -160,36 +160,44 @@ __global__ void k_block_inv(const double* __restrict__ LBall, double* __restrict
 
 // ---------------------------------------------------------------- substitution
 // Software-pipelined blocked substitution.  While the triangle warp (warp
-// kTri) finishes block b -- the coupling to the previous block, the
+// Shape<NT>::TRI) finishes block b -- the coupling to the previous block, the
 // reduction of the partial sums and the product with the inverted diagonal
 // block -- the other warps compute the partial sums of block b+1 against all
 // columns solved before block b and stage the 32 x 32 coupling between blocks
 // b+1 and b into shared memory.
-constexpr int kTri = kDW - 1;
-constexpr int kGemvWarps = kDW - 1;
+// NT threads per CTA: warps 0 .. NT/32-2 compute the partial sums, the last
+// warp is the triangle warp.
+template <int NT>
+struct Shape {
+  static constexpr int DW = NT / 32;
+  static constexpr int TRI = DW - 1;
+  static constexpr int GW = DW - 1;
+  static_assert(DW >= 2 && DW <= kBlk, "2 to 32 warps");
+};
 
 struct SolveSmem {
   double part[2][kBlk][kBlk + 1];   // [buffer][row][lane] partial sums
   double off[2][kBlk][kBlk + 1];    // [buffer][row][col] coupling block
   double sacc[kBlk];
-  double red[kDW];
+  double red[32];
 };
 
 // L~ y = w in place (w already scaled by D^-1, permuted order).
+template <int NT>
 __device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                               int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kBlk - 1) / kBlk;
   // block 0 has no solved columns: empty partial sums and coupling
-  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += kDT) {
+  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += NT) {
     (&sm.part[0][0][0])[t] = 0.0;
     (&sm.off[0][0][0])[t] = 0.0;
   }
   __syncthreads();
   for (int b = 0; b < nblk; ++b) {
     const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
-    if (warp == kTri) {
+    if (warp == Shape<NT>::TRI) {
       const int i = i0 + lane;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
@@ -223,7 +231,7 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
     } else if (b + 1 < nblk) {
       // block b+1 against the columns solved before block b: [i - bw, i0)
       const int j0 = i0 + kBlk;
-      for (int r = warp; r < kBlk; r += kGemvWarps) {
+      for (int r = warp; r < kBlk; r += Shape<NT>::GW) {
         const int i = j0 + r;
         double acc = 0.0;
         if (i < n) {
@@ -252,19 +260,20 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
 }
 
 // L~^T u = w in place, from the last block up.
+template <int NT>
 __device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
                                int n, int bw, double* w, SolveSmem& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kBlk - 1) / kBlk;
-  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += kDT) {
+  for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += NT) {
     (&sm.part[(nblk - 1) & 1][0][0])[t] = 0.0;
     (&sm.off[(nblk - 1) & 1][0][0])[t] = 0.0;
   }
   __syncthreads();
   for (int b = nblk - 1; b >= 0; --b) {
     const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
-    if (warp == kTri) {
+    if (warp == Shape<NT>::TRI) {
       const int i = i0 + lane;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
@@ -306,25 +315,26 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
       double acc = 0.0;
       const int kend = min(n - 1, j0 + kBlk - 1 + bw);
       int k = i0 + kBlk + warp;
-      for (; k + 3 * kGemvWarps <= kend && k + 3 * kGemvWarps - j0 <= bw; k += 4 * kGemvWarps) {
+      for (; k + 3 * Shape<NT>::GW <= kend && k + 3 * Shape<NT>::GW - j0 <= bw; k += 4 * Shape<NT>::GW) {
         const double* r0 = LB + (int64_t)k * W + (col - k + bw);
-        const double l0 = r0[0], l1 = r0[kGemvWarps * (W - 1)], l2 = r0[2 * kGemvWarps * (W - 1)],
-                     l3 = r0[3 * kGemvWarps * (W - 1)];
-        const double w0 = w[k], w1 = w[k + kGemvWarps], w2 = w[k + 2 * kGemvWarps],
-                     w3 = w[k + 3 * kGemvWarps];
+        const double l0 = r0[0], l1 = r0[Shape<NT>::GW * (W - 1)], l2 = r0[2 * Shape<NT>::GW * (W - 1)],
+                     l3 = r0[3 * Shape<NT>::GW * (W - 1)];
+        const double w0 = w[k], w1 = w[k + Shape<NT>::GW], w2 = w[k + 2 * Shape<NT>::GW],
+                     w3 = w[k + 3 * Shape<NT>::GW];
         acc = fma(l0, w0, acc);
         acc = fma(l1, w1, acc);
         acc = fma(l2, w2, acc);
         acc = fma(l3, w3, acc);
       }
-      for (; k <= kend; k += kGemvWarps) {
+      for (; k <= kend; k += Shape<NT>::GW) {
         const int off = col - k + bw;
         if (off >= 0) acc = fma(LB[(int64_t)k * W + off], w[k], acc);
       }
       sm.part[nxt][warp][lane] = acc;
-      if (warp == 0) sm.part[nxt][kBlk - 1][lane] = 0.0;   // slot of the triangle warp
+      if (warp == 0)   // slots without a partial-sum warp
+        for (int q = Shape<NT>::GW; q < kBlk; ++q) sm.part[nxt][q][lane] = 0.0;
       // coupling rows i0 + r (block b) x column j0 + lane (block b-1)
-      for (int r = warp; r < kBlk; r += kGemvWarps) {
+      for (int r = warp; r < kBlk; r += Shape<NT>::GW) {
         const int kk = i0 + r;
         sm.off[nxt][r][lane] = (kk < n && kk - col <= bw) ? LB[(int64_t)kk * W + (col - kk + bw)] : 0.0;
       }
@@ -349,6 +359,7 @@ struct DLaneOut {
 
 // Advance one lane by n_steps implicit-Euler steps with the direct solver.
 // On return the final state is in a0 (as given).
+template <int NT>
 __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int n_steps,
                                  int64_t k0, SolveSmem& sm, DLaneOut& out) {
   const int n = kc.n;
@@ -360,9 +371,9 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
   const double* Mv = kc.M + D.vcol;
   const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
   if (D.init_from_a0) {
-    for (int i = threadIdx.x; i < n; i += kDT) y[i] = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a0);
+    for (int i = threadIdx.x; i < n; i += NT) y[i] = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a0);
   } else {
-    for (int i = threadIdx.x; i < n; i += kDT) {
+    for (int i = threadIdx.x; i < n; i += NT) {
       a0[i] = 0.0;
       y[i] = 0.0;
     }
@@ -381,7 +392,7 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
         g[ph] = D.amp[ph] * sin(arg);
       }
     }
-    for (int i = threadIdx.x; i < n; i += kDT) {
+    for (int i = threadIdx.x; i < n; i += NT) {
       double f = 0.0;
 #pragma unroll
       for (int ph = 0; ph < kMaxPhases; ++ph)
@@ -390,15 +401,15 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
       w[pi] = (y[i] / dt + f) * D.invd[pi];          // D^-1 b
     }
     __syncthreads();
-    forward_subst(D.LB, D.Binv, n, kc.bw, w, sm);
-    backward_subst(D.LB, D.Binv, n, kc.bw, w, sm);
-    for (int i = threadIdx.x; i < n; i += kDT) {
+    forward_subst<NT>(D.LB, D.Binv, n, kc.bw, w, sm);
+    backward_subst<NT>(D.LB, D.Binv, n, kc.bw, w, sm);
+    for (int i = threadIdx.x; i < n; i += NT) {
       const int pi = __ldg(kc.iperm + i);
       a1[i] = w[pi] * D.invd[pi];                     // x = D^-1 u
     }
     __syncthreads();
     double part = 0.0;
-    for (int i = threadIdx.x; i < n; i += kDT) {
+    for (int i = threadIdx.x; i < n; i += NT) {
       const double yn = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a1);
       if (kc.qoi_kind == MQS_QOI_JOULE) {
         part = fma(a1[i] - a0[i], yn - y[i], part);
@@ -407,7 +418,7 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
       }
       y[i] = yn;
     }
-    const double red = block_sum(part, sm.red);
+    const double red = block_sum<NT>(part, sm.red);
     qacc += kc.qoi_kind == MQS_QOI_JOULE ? red / dt : 0.5 * red;
     double* tmp = a0;
     a0 = a1;
@@ -415,24 +426,26 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
     __syncthreads();
   }
   if (n_steps & 1) {
-    for (int i = threadIdx.x; i < n; i += kDT) a1[i] = a0[i];
+    for (int i = threadIdx.x; i < n; i += NT) a1[i] = a0[i];
     __syncthreads();
   }
   out.qoi = qacc;
 }
 
-__global__ void __launch_bounds__(kDT) k_direct_propagate(const DirectLane* __restrict__ lanes,
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_direct_propagate(const DirectLane* __restrict__ lanes,
                                                          DirectConst kc) {
   __shared__ SolveSmem sm;
   const DirectLane D = lanes[blockIdx.x];
   DLaneOut out;
-  direct_integrate(kc, D, D.n_steps, D.k0, sm, out);
+  direct_integrate<NT>(kc, D, D.n_steps, D.k0, sm, out);
   if (threadIdx.x == 0) D.qoi_out[0] = out.qoi;
 }
 
 // Parareal coarse sweep, one CTA per sample; slice states lane-major
 // U/E/G[(sample*M + s) * n + i].
-__global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restrict__ lanes,
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_direct_chain(const DirectLane* __restrict__ lanes,
                                                      DirectConst kc, DirectChain ch) {
   __shared__ SolveSmem sm;
   DirectLane D = lanes[blockIdx.x];
@@ -441,12 +454,12 @@ __global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restri
   D.init_from_a0 = 1;
   for (int s = ch.s_begin; s < ch.M - 1; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
-    for (int i = threadIdx.x; i < n; i += kDT) D.a0[i] = ch.U[base + i];
+    for (int i = threadIdx.x; i < n; i += NT) D.a0[i] = ch.U[base + i];
     __syncthreads();
     DLaneOut out;
-    direct_integrate(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
+    direct_integrate<NT>(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
     double j2 = 0.0, u2 = 0.0;
-    for (int i = threadIdx.x; i < n; i += kDT) {
+    for (int i = threadIdx.x; i < n; i += NT) {
       const double gn = D.a0[i];
       const double un = ch.first_sweep ? gn : ch.E[base + i] + (gn - ch.G[base + i]);
       const double du = un - ch.U[base + n + i];
@@ -455,8 +468,8 @@ __global__ void __launch_bounds__(kDT) k_direct_chain(const DirectLane* __restri
       ch.U[base + n + i] = un;
       ch.G[base + i] = gn;
     }
-    j2 = block_sum(j2, sm.red);
-    u2 = block_sum(u2, sm.red);
+    j2 = block_sum<NT>(j2, sm.red);
+    u2 = block_sum<NT>(u2, sm.red);
     if (threadIdx.x == 0) {
       ch.jump2[(int64_t)sample * ch.M + s + 1] = j2;
       ch.norm2[(int64_t)sample * ch.M + s + 1] = u2;
@@ -514,27 +527,46 @@ size_t direct_smem(const DirectConst& kc) {
   return kc.w_in_smem ? (size_t)kc.n * sizeof(double) : 0;
 }
 
-int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
-  if (n_lanes <= 0) return MQS_OK;
+// Threads per lane-CTA: 1024 with the work vector in shared memory (one lane
+// per SM) when the lanes do not fill the GPU; 256 with the work vector in L2
+// for large batches, so that several lanes per SM overlap their latencies.
+int direct_threads(const DirectConst& kc) { return kc.w_in_smem ? 1024 : 256; }
+
+template <int NT>
+int launch_direct_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                    cudaStream_t st) {
   const size_t smem = direct_smem(kc);   // on top of the static SolveSmem
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate,
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate<NT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_direct_propagate<<<n_lanes, kDT, smem, st>>>(d_lanes, kc);
+  k_direct_propagate<NT><<<n_lanes, NT, smem, st>>>(d_lanes, kc);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
 }
 
-int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
-                        const DirectChain& ch, cudaStream_t st) {
-  if (n_lanes <= 0) return MQS_OK;
+template <int NT>
+int launch_chain_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                   const DirectChain& ch, cudaStream_t st) {
   const size_t smem = direct_smem(kc);
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  k_direct_chain<<<n_lanes, kDT, smem, st>>>(d_lanes, kc, ch);
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain<NT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_direct_chain<NT><<<n_lanes, NT, smem, st>>>(d_lanes, kc, ch);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
+}
+
+int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  return direct_threads(kc) == 1024 ? launch_direct_t<1024>(d_lanes, n_lanes, kc, st)
+                                    : launch_direct_t<256>(d_lanes, n_lanes, kc, st);
+}
+
+int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                        const DirectChain& ch, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  return direct_threads(kc) == 1024 ? launch_chain_t<1024>(d_lanes, n_lanes, kc, ch, st)
+                                    : launch_chain_t<256>(d_lanes, n_lanes, kc, ch, st);
 }
 
 }  // namespace mqs
