@@ -57,6 +57,12 @@ def workload(name):
         return dict(name="parareal_annulus20k_short", mesh=meshes.annulus("20k"),
                     params=params.annulus_nominal(1), t_end=256 * c.dt, dt=c.dt, n_steps=256,
                     n_slices=c.n_slices, cf=4, par_tol=c.tol, qoi=c.qoi, cg_tol=1e-12)
+    if name == "mlmc20k":
+        c = configs.MLMC_ANNULUS
+        return dict(name="mlmc_annulus20k", mesh=meshes.annulus("20k"), mlmc=c,
+                    params=[params.annulus_samples(n, l) for l, n in enumerate(c.n_per_level)],
+                    t_end=c.periods * configs.PERIOD, qoi=c.qoi, cg_tol=1e-12,
+                    n_steps=None, dt=configs.level_dt(0), n_slices=1, cf=1, par_tol=0.0)
     if name == "mcsquare":
         c = configs.MC_SQUARE
         return dict(name="mc_square16", mesh=meshes.unit_square(16),
@@ -385,6 +391,67 @@ def run_ours(args, wl, rank, world, dist):
     ctx.close()
 
 
+def run_mlmc(args, wl):
+    """One MLMC estimate (Eq. 9) per step: every level's samples, both solves
+    of each level pair, moments, readout; time-to-RMSE from upload to readout."""
+    import numpy as np
+    import torch
+
+    from paper_2507_19246_gb300 import mqs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = mqs.Context(0, stream.cuda_stream)
+    from workloads import configs
+    c = wl["mlmc"]
+    mesh_id = ctx.upload_mesh(wl["mesh"])
+    n_free, nnz = ctx.mesh_info(mesh_id)
+    prec = mqs.MQS_MIXED if args.precision == "mixed" else mqs.MQS_FP64
+    p_dev = [torch.from_numpy(p).cuda() for p in wl["params"]]
+    chunk = 1024
+    L = c.n_levels
+
+    def estimate():
+        mqs.mqs_mlmc_reset(ctx.h, L)
+        for l, N in enumerate(c.n_per_level):
+            for s0 in range(0, N, chunk):
+                b = mqs.mqs_set_samples(ctx.h, mesh_id, p_dev[l][s0:s0 + chunk])
+                if args.solver == "banded":
+                    mqs.mqs_set_solver(ctx.h, b, mqs.MQS_SOLVER_BANDED)
+                mqs.mqs_set_time(ctx.h, b, 0.0, wl["t_end"], 50.0, wl["qoi"])
+                mqs.mqs_propagate(ctx.h, b, l, configs.level_dt(l),
+                                  configs.level_dt(l - 1) if l else 0.0, 1, 1, 1, 0.0, prec,
+                                  1e-12 if prec == mqs.MQS_FP64 else 1e-9, 20000)
+                mqs.mqs_mlmc_accumulate(ctx.h, b, l)
+                mqs.mqs_free_batch(ctx.h, b)
+        return mqs.mqs_mlmc_readout(ctx.h, L)
+
+    for _ in range(args.warmup):
+        estimate()
+    torch.cuda.synchronize()
+    times, res = [], None
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            res = estimate()
+            times.append(time.perf_counter() - t0)
+    lv, est, rmse = res
+    units = c.solve_steps() * n_free
+    line = {"metric": "sample-DoF-steps/s", "value": units * len(times) / sum(times),
+            "unit": "sample-DoF-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "n_free": n_free, "levels": L,
+                       "n_per_level": list(c.n_per_level), "periods": c.periods,
+                       "solver": args.solver, "precision": args.precision,
+                       "solve_steps": c.solve_steps()},
+            "time_to_rmse_s": statistics.median(times), "estimate": est, "rmse": rmse,
+            "levels": lv.tolist(), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,7 +459,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare"])
+    ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare", "mlmc20k"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "banded"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -400,6 +467,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     dist = None
     wl = workload(args.workload)
+    if args.workload == "mlmc20k" and args.impl != "reference":
+        run_mlmc(args, wl)
+        return
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
         return
