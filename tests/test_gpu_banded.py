@@ -55,7 +55,11 @@ def test_banded_square_energy_full_config(ctx, mqs):
         assert abs(q[s, 0] - qo) <= TOL * abs(qo) and _rel(a[s], ao) <= TOL
 
 
-def test_banded_level_pair_ragged_annulus(ctx, mqs):
+@pytest.mark.parametrize("wide", ["1", "0"])
+def test_banded_level_pair_ragged_annulus(ctx, mqs, monkeypatch, wide):
+    # wide = 1: 1024-thread lane CTAs, work vector in shared memory;
+    # wide = 0: 256-thread lane CTAs (4 per SM), work vector in global memory
+    monkeypatch.setenv("MQS_DIRECT_WIDE", wide)
     mesh = meshes.annulus("5k")
     p = params.annulus_samples(37, 1)
     dt1, dt0 = configs.level_dt(1), configs.level_dt(0)
