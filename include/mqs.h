@@ -47,7 +47,7 @@ extern "C" {
 
 /* linear solver of the implicit-Euler systems (mqs_set_solver) */
 #define MQS_SOLVER_PCG    0  /* batched Jacobi-preconditioned CG (default) */
-#define MQS_SOLVER_BANDED 1  /* band Cholesky in reverse Cuthill-McKee order, FP64 */
+#define MQS_SOLVER_BANDED 1  /* band Cholesky in reverse Cuthill-McKee order */
 
 /* quantity of interest */
 #define MQS_QOI_ENERGY 0  /* (1/N) sum_{k=1..N} 1/2 a_k^T K a_k (time-averaged magnetic energy) */
@@ -122,8 +122,11 @@ int mqs_set_time(mqs_ctx* ctx, int32_t batch_id, double t0, double t_end,
  * (M/dt + K) a_{k+1} = b each step.  The banded solver factors M/dt + K once
  * per sample and step size (band Cholesky after a reverse Cuthill-McKee
  * ordering of the free unknowns, n x (bw+1) doubles per factor) and then does
- * one forward and one backward substitution per step.  It has no iteration
- * tolerance (cg_tol, cg_max_iters are ignored) and supports MQS_FP64 only. */
+ * one forward and one backward substitution per step.  MQS_FP64: the factor
+ * and the substitutions are FP64 (cg_tol and cg_max_iters are ignored).
+ * MQS_MIXED: the factor and substitutions are FP32 and each step refines in
+ * FP64 -- residual r = b - A x with the FP64 matrix, x += (L L^T)^-1 r --
+ * until ||r||_2 <= cg_tol ||b||_2 or cg_max_iters sweeps (MQS_ST_NOTCONV). */
 int mqs_set_solver(mqs_ctx* ctx, int32_t batch_id, int32_t solver);
 
 /* Bandwidth of a mesh's reverse Cuthill-McKee ordering (used by the banded solver). */

@@ -41,22 +41,26 @@ struct ValueSet {
 
 struct FactorSet {
   double dt = 0.0;
+  bool have64 = false, have32 = false;
   DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
+  DevBuf LBf, invdf, Binvf;     // FP32 factor (mixed precision)
 };
 
 // Lanes of the banded direct solver: one CTA per lane, vectors lane-major.
 struct DirectSet {
   int lanes = 0, n = 0;
-  DevBuf vec, qraw, desc;
+  DevBuf vec, qraw, status, desc;
   std::vector<DirectLane> host;
   int ensure(int lanes_, int n_) {
     lanes = lanes_;
     n = n_;
-    MQS_TRY(vec.ensure((size_t)lanes * 4 * n * sizeof(double)));
+    MQS_TRY(vec.ensure((size_t)lanes * 5 * n * sizeof(double)));
     MQS_TRY(qraw.ensure((size_t)lanes * sizeof(double)));
+    MQS_TRY(status.ensure((size_t)lanes * sizeof(int32_t)));
     return MQS_OK;
   }
-  double* v(int lane, int j) const { return vec.as<double>() + ((size_t)lane * 4 + j) * n; }
+  // vectors of a lane: 0 a0, 1 a1, 2 y, 3 work (permuted), 4 b (mixed)
+  double* v(int lane, int j) const { return vec.as<double>() + ((size_t)lane * 5 + j) * n; }
 };
 
 struct LaneSet {
@@ -550,29 +554,46 @@ int run_parareal(mqs_ctx* ctx, Batch& b, const MeshDev& m, const ValueSet& vf,
 }
 
 
-FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, int& rc) {
+FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool mixed, int& rc) {
   rc = MQS_OK;
-  for (auto& f : b.fsets)
-    if (f->dt == dt) return f.get();
+  FactorSet* f = nullptr;
+  for (auto& x : b.fsets)
+    if (x->dt == dt) f = x.get();
+  if (f && (mixed ? f->have32 : f->have64)) return f;
   ValueSet* v = value_set(ctx, b, m, dt, false, rc);
   if (!v) return nullptr;
-  b.fsets.emplace_back(new FactorSet());
-  FactorSet* f = b.fsets.back().get();
-  f->dt = dt;
+  if (!f) {
+    b.fsets.emplace_back(new FactorSet());
+    f = b.fsets.back().get();
+    f->dt = dt;
+  }
   const size_t fstride = (size_t)m.n_free * (m.bw + 1);
-  if ((rc = f->LB.ensure(fstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
-  if ((rc = f->invd.ensure((size_t)m.n_free * b.n * sizeof(double))) != MQS_OK) return nullptr;
-  if ((rc = f->bad.ensure((size_t)b.n * sizeof(int32_t))) != MQS_OK) return nullptr;
   const size_t bstride = (size_t)block_count(m.n_free) * 32 * 32;
-  if ((rc = f->Binv.ensure(bstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
-  rc = band_factor(m, v->A.as<double>(), b.n, b.n, f->LB.as<double>(), f->invd.as<double>(),
-                   f->Binv.as<double>(), f->bad.as<int32_t>(), ctx->c.stream);
+  if ((rc = f->bad.ensure((size_t)b.n * sizeof(int32_t))) != MQS_OK) return nullptr;
+  if (mixed) {
+    if ((rc = f->LBf.ensure(fstride * b.n * sizeof(float))) != MQS_OK) return nullptr;
+    if ((rc = f->invdf.ensure((size_t)m.n_free * b.n * sizeof(float))) != MQS_OK) return nullptr;
+    if ((rc = f->Binvf.ensure(bstride * b.n * sizeof(float))) != MQS_OK) return nullptr;
+    rc = band_factor<float>(m, v->A.as<double>(), b.n, b.n, f->LBf.as<float>(),
+                            f->invdf.as<float>(), f->Binvf.as<float>(), f->bad.as<int32_t>(),
+                            ctx->c.stream);
+    f->have32 = rc == MQS_OK;
+  } else {
+    if ((rc = f->LB.ensure(fstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
+    if ((rc = f->invd.ensure((size_t)m.n_free * b.n * sizeof(double))) != MQS_OK) return nullptr;
+    if ((rc = f->Binv.ensure(bstride * b.n * sizeof(double))) != MQS_OK) return nullptr;
+    rc = band_factor<double>(m, v->A.as<double>(), b.n, b.n, f->LB.as<double>(),
+                             f->invd.as<double>(), f->Binv.as<double>(), f->bad.as<int32_t>(),
+                             ctx->c.stream);
+    f->have64 = rc == MQS_OK;
+  }
   return rc == MQS_OK ? f : nullptr;
 }
 
 // lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
 // vector in L2, several per SM (env MQS_DIRECT_WIDE=1/0 forces a choice).
-DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm) {
+DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, bool mixed,
+                         double tol, int max_sweeps) {
   DirectConst kc;
   memset(&kc, 0, sizeof(kc));
   kc.rowptr = m.rowptr.as<int32_t>();
@@ -589,19 +610,30 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm) 
   kc.omega = kTwoPi * b.freq;
   const int forced = env_int("MQS_DIRECT_WIDE", -1);
   const bool wide = forced >= 0 ? forced == 1 : lanes < 2 * n_sm;
-  kc.w_in_smem = (wide && m.n_free <= direct_smem_max_n()) ? 1 : 0;
+  kc.w_in_smem = (wide && m.n_free <= direct_smem_max_n(mixed ? 1 : 0)) ? 1 : 0;
+  kc.mixed = mixed ? 1 : 0;
+  kc.tol2 = tol * tol;
+  kc.max_sweeps = max_sweeps;
   return kc;
 }
 
 DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int sample,
-                       double* a0, double* a1, double* y, double* w, double* qoi_out,
-                       int n_steps, int64_t k0, int init_from_a0) {
+                       double* a0, double* a1, double* y, double* w, double* rhs,
+                       double* qoi_out, int32_t* status_out, int n_steps, int64_t k0,
+                       int init_from_a0) {
   DirectLane d;
   memset(&d, 0, sizeof(d));
   const size_t fstride = (size_t)m.n_free * (m.bw + 1);
   d.LB = f.LB.as<double>() + fstride * sample;
   d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
   d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  d.LBf = f.LBf.as<float>() + fstride * sample;
+  d.invdf = f.invdf.as<float>() + (size_t)m.n_free * sample;
+  d.Binvf = f.Binvf.as<float>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  for (auto& v : b.vsets)
+    if (v->dt == f.dt) d.Av = v->A.as<double>() + sample;
+  d.b = rhs;
+  d.status_out = status_out;
   d.a0 = a0;
   d.a1 = a1;
   d.y = y;
@@ -633,23 +665,26 @@ int upload_direct(mqs_ctx* ctx, DirectSet& ds) {
 
 // Sequential stepping with the banded solver: lanes [0, nf) level l, [nf, nf+nc) level l-1.
 int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* ff, int nsf,
-                     const FactorSet* fc, int nsc) {
+                     const FactorSet* fc, int nsc, bool mixed, double tol, int max_sweeps) {
   const int nf = ff ? b.n : 0, nc = fc ? b.n : 0;
   DirectSet& ds = b.dplain;
   MQS_TRY(ds.ensure(nf + nc, m.n_free));
   MQS_CUDA_TRY(cudaMemsetAsync(ds.qraw.p, 0, (size_t)(nf + nc) * sizeof(double), ctx->c.stream));
+  MQS_CUDA_TRY(cudaMemsetAsync(ds.status.p, 0, (size_t)(nf + nc) * sizeof(int32_t), ctx->c.stream));
   ds.host.clear();
   for (int s = 0; s < nf; ++s)
     ds.host.push_back(direct_lane(m, b, *ff, s, ds.v(s, 0), ds.v(s, 1), ds.v(s, 2), ds.v(s, 3),
-                                  ds.qraw.as<double>() + s, nsf, 0, 0));
+                                  ds.v(s, 4), ds.qraw.as<double>() + s,
+                                  ds.status.as<int32_t>() + s, nsf, 0, 0));
   for (int s = 0; s < nc; ++s) {
     const int l = nf + s;
     ds.host.push_back(direct_lane(m, b, *fc, s, ds.v(l, 0), ds.v(l, 1), ds.v(l, 2), ds.v(l, 3),
-                                  ds.qraw.as<double>() + l, nsc, 0, 0));
+                                  ds.v(l, 4), ds.qraw.as<double>() + l,
+                                  ds.status.as<int32_t>() + l, nsc, 0, 0));
   }
   b.nf_direct = nf;
   MQS_TRY(upload_direct(ctx, ds));
-  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm);
+  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm, mixed, tol, max_sweeps);
   MQS_TRY(prof_mark(ctx->c, 0, true));
   MQS_TRY(launch_direct(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
   MQS_TRY(prof_mark(ctx->c, 0, false));
@@ -661,7 +696,7 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* 
 
 int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet& fF,
                         const FactorSet& fC, int n_steps, int M, int cf, int max_iters, double tol,
-                        int& iters_out) {
+                        bool mixed, double ir_tol, int max_sweeps, int& iters_out) {
   const cudaStream_t st = ctx->c.stream;
   const int S = n_steps / M, Sc = S / cf, ns = b.n, n = m.n_free;
   const int lanes = ns * M;
@@ -677,13 +712,16 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
   MQS_CUDA_TRY(cudaMemsetAsync(b.G.p, 0, field, st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.norm2.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.qraw.p, 0, (size_t)lanes * sizeof(double), st));
-  const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm);
-  const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm);
+  MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.status.p, 0, (size_t)lanes * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
+  const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
+  const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
   DirectSet& dc = b.dchain;
   dc.host.clear();
   for (int s = 0; s < ns; ++s)
     dc.host.push_back(direct_lane(m, b, fC, s, dc.v(s, 0), dc.v(s, 1), dc.v(s, 2), dc.v(s, 3),
-                                  dc.qraw.as<double>() + s, Sc, 0, 1));
+                                  dc.v(s, 4), dc.qraw.as<double>() + s,
+                                  dc.status.as<int32_t>() + s, Sc, 0, 1));
   MQS_TRY(upload_direct(ctx, dc));
   DirectChain ch;
   ch.U = b.U.as<double>();
@@ -710,7 +748,8 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
       for (int j = k - 1; j < M; ++j) {
         const int l = s * M + j, c = (int)dp.host.size();
         dp.host.push_back(direct_lane(m, b, fF, s, b.E.as<double>() + (size_t)l * n, dp.v(c, 1),
-                                      dp.v(c, 2), dp.v(c, 3), dp.qraw.as<double>() + l, S,
+                                      dp.v(c, 2), dp.v(c, 3), dp.v(c, 4),
+                                      dp.qraw.as<double>() + l, dp.status.as<int32_t>() + l, S,
                                       (int64_t)j * S, 1));
       }
     fine_steps += (double)dp.host.size() * S;
@@ -1082,14 +1121,14 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
   MQS_TRY(ensure_mk(ctx, b, m));
   int rc = MQS_OK;
   if (b.solver == MQS_SOLVER_BANDED) {
-    if (mixed || m.bw < 0) {
-      set_error("the banded solver supports MQS_FP64 only and needs n_free * (bw + 1) < 2^31");
+    if (m.bw < 0) {
+      set_error("the banded solver needs n_free * (bw + 1) < 2^31");
       return MQS_EINVAL;
     }
-    FactorSet* ff = factor_set(ctx, b, m, dt_level, rc);
+    FactorSet* ff = factor_set(ctx, b, m, dt_level, mixed, rc);
     if (!ff) return rc;
     FactorSet* fc = nullptr;
-    if (dt_prev > 0.0 && !(fc = factor_set(ctx, b, m, dt_prev, rc))) return rc;
+    if (dt_prev > 0.0 && !(fc = factor_set(ctx, b, m, dt_prev, mixed, rc))) return rc;
     b.level = level;
     b.has_coarse = fc != nullptr;
     for (double& x : b.stats) x = 0.0;
@@ -1097,7 +1136,7 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
     int par_iters = 0;
     const cudaStream_t st = ctx->c.stream;
     if (n_slices == 1) {
-      MQS_TRY(run_plain_direct(ctx, b, m, ff, nsf, fc, nsc));
+      MQS_TRY(run_plain_direct(ctx, b, m, ff, nsf, fc, nsc, mixed, cg_tol, cg_max_iters));
       b.mode = 3;
       b.M = 1;
       MQS_TRY(finish_qoi(b.dplain.qraw.as<double>(),
@@ -1105,11 +1144,13 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
                          qoi_scale(b.qoi_kind, nsf, dt_level),
                          fc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
     } else {
-      if (fc) MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc));
-      FactorSet* fC = factor_set(ctx, b, m, dt_level * coarse_factor, rc);
+      if (fc)
+        MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc, mixed, cg_tol, cg_max_iters));
+      FactorSet* fC = factor_set(ctx, b, m, dt_level * coarse_factor, mixed, rc);
       if (!fC) return rc;
       MQS_TRY(run_parareal_direct(ctx, b, m, *ff, *fC, nsf, n_slices, coarse_factor,
-                                  max_par_iters, par_tol, par_iters));
+                                  max_par_iters, par_tol, mixed, cg_tol, cg_max_iters,
+                                  par_iters));
       b.mode = 4;
       b.M = n_slices;
       MQS_TRY(finish_qoi(b.dpar.qraw.as<double>(), fc ? b.dplain.qraw.as<double>() : nullptr,
@@ -1189,6 +1230,23 @@ int mqs_read_qoi(mqs_ctx* ctx, int32_t batch_id, double* qoi, int32_t* status) {
       MQS_TRY(fold(b->chain, b->n, 1, 0));
       if (b->has_coarse) MQS_TRY(fold(b->plain, b->n, 1, 0));
     } else if (b->mode >= 3) {
+      auto fold_direct = [&](const DirectSet& ds, int lanes, int lps, int off) -> int {
+        if (lanes <= 0) return MQS_OK;
+        std::vector<int32_t> hs((size_t)lanes);
+        MQS_CUDA_TRY(cudaMemcpyAsync(hs.data(), ds.status.as<int32_t>() + off,
+                                     lanes * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MQS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int l = 0; l < lanes; ++l) out[l / lps] |= hs[l];
+        return MQS_OK;
+      };
+      if (b->mode == 3) {
+        MQS_TRY(fold_direct(b->dplain, b->n, 1, 0));
+        if (b->has_coarse) MQS_TRY(fold_direct(b->dplain, b->n, 1, b->nf_direct));
+      } else {
+        MQS_TRY(fold_direct(b->dpar, b->n * b->M, b->M, 0));
+        MQS_TRY(fold_direct(b->dchain, b->n, 1, 0));
+        if (b->has_coarse) MQS_TRY(fold_direct(b->dplain, b->n, 1, 0));
+      }
       // a non-positive pivot in any factor of the sample
       std::vector<int32_t> h((size_t)b->n);
       for (auto& f : b->fsets) {
@@ -1233,7 +1291,7 @@ int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a) {
     } else {
       const int lane0 = which == 0 ? 0 : b->nf_direct;
       src = b->dplain.v(lane0, 0);
-      pitch = row * 4;
+      pitch = row * 5;
     }
     MQS_CUDA_TRY(cudaMemcpy2DAsync(out, row, src, pitch, row, b->n, cudaMemcpyDeviceToDevice, st));
   } else if (which == 0 && b->mode == 2) {

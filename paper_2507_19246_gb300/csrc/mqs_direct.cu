@@ -54,45 +54,48 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+template <typename T>
 __global__ void k_band_fill(int64_t nnz, const int32_t* __restrict__ band_idx,
                             const double* __restrict__ A, int64_t vs, int n_fac,
-                            int64_t fstride, double* __restrict__ LB) {
+                            int64_t fstride, T* __restrict__ LB) {
   const int64_t total = nnz * n_fac;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = t / n_fac;
     const int f = (int)(t % n_fac);
     const int32_t b = band_idx[k];
-    if (b >= 0) LB[f * fstride + b] = A[k * vs + f];
+    if (b >= 0) LB[f * fstride + b] = (T)A[k * vs + f];
   }
 }
 
-__global__ void __launch_bounds__(kDT) k_band_chol(double* __restrict__ LBall,
-                                                  double* __restrict__ invd_all, int n, int bw,
+template <typename T>
+__global__ void __launch_bounds__(kDT) k_band_chol(T* __restrict__ LBall,
+                                                  T* __restrict__ invd_all, int n, int bw,
                                                   int64_t fstride, int32_t* __restrict__ bad) {
-  extern __shared__ double colj[];   // bw entries of the current column
-  __shared__ double s_inv;
-  double* LB = LBall + blockIdx.x * fstride;
-  double* invd = invd_all + (int64_t)blockIdx.x * n;
+  extern __shared__ unsigned char colj_raw[];
+  T* colj = reinterpret_cast<T*>(colj_raw);   // bw entries of the current column
+  __shared__ T s_inv;
+  T* LB = LBall + blockIdx.x * fstride;
+  T* invd = invd_all + (int64_t)blockIdx.x * n;
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
-      double d = LB[(int64_t)j * W + bw];
-      if (!(d > 0.0)) {   // not positive definite: record and continue on a unit pivot
+      T d = LB[(int64_t)j * W + bw];
+      if (!(d > T(0))) {   // not positive definite: record and continue on a unit pivot
         bad[blockIdx.x] = 1;
-        d = 1.0;
+        d = T(1);
       }
       d = sqrt(d);
       LB[(int64_t)j * W + bw] = d;
-      s_inv = 1.0 / d;
+      s_inv = T(1) / d;
       invd[j] = s_inv;
     }
     __syncthreads();
-    const double inv = s_inv;
+    const T inv = s_inv;
     for (int t = threadIdx.x; t < bw; t += kDT) {
       const int i = j + 1 + t;
-      double v = 0.0;
+      T v = T(0);
       if (i < n) {
         const int64_t o = (int64_t)i * W + (j - i + bw);
         v = LB[o] * inv;
@@ -105,9 +108,9 @@ __global__ void __launch_bounds__(kDT) k_band_chol(double* __restrict__ LBall,
     for (int a = warp; a < bw; a += kDW) {
       const int i = j + 1 + a;
       if (i >= n) break;
-      const double ca = colj[a];
-      if (ca == 0.0) continue;
-      double* row = LB + (int64_t)i * W + (j + 1 - i + bw);   // column j+1 of row i
+      const T ca = colj[a];
+      if (ca == T(0)) continue;
+      T* row = LB + (int64_t)i * W + (j + 1 - i + bw);   // column j+1 of row i
       for (int b = lane; b <= a; b += 32) row[b] = fma(-ca, colj[b], row[b]);
     }
     __syncthreads();
@@ -120,33 +123,35 @@ __global__ void __launch_bounds__(kDT) k_band_chol(double* __restrict__ LBall,
 // L~^T u = y with x = D^-1 u.  The inverse of every 32 x 32 diagonal block of
 // L~ is stored as well, which turns the sequential in-block substitution into
 // a small dense product.
-__global__ void k_band_unit(double* __restrict__ LBall, const double* __restrict__ invd_all,
+template <typename T>
+__global__ void k_band_unit(T* __restrict__ LBall, const T* __restrict__ invd_all,
                             int n, int bw, int64_t fstride, int n_fac) {
   const int W = bw + 1;
   const int64_t total = (int64_t)n * n_fac;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; t < total;
        t += (int64_t)gridDim.x * blockDim.y) {
     const int f = (int)(t / n), i = (int)(t % n);
-    double* row = LBall + f * fstride + (int64_t)i * W;
-    const double s = invd_all[(int64_t)f * n + i];
+    T* row = LBall + f * fstride + (int64_t)i * W;
+    const T s = invd_all[(int64_t)f * n + i];
     for (int d = threadIdx.x; d < bw; d += blockDim.x) row[d] *= s;
-    if (threadIdx.x == 0) row[bw] = 1.0;
+    if (threadIdx.x == 0) row[bw] = T(1);
   }
 }
 
 // One warp per diagonal block: lane c solves L~_blk x = e_c (rows past n are identity).
-__global__ void k_block_inv(const double* __restrict__ LBall, double* __restrict__ Binv_all,
+template <typename T>
+__global__ void k_block_inv(const T* __restrict__ LBall, T* __restrict__ Binv_all,
                             int n, int bw, int64_t fstride, int nblk, int n_fac) {
-  __shared__ double xs[4][kBlk][kBlk + 1];
+  __shared__ T xs[4][kBlk][kBlk + 1];
   const int wl = threadIdx.x >> 5, c = threadIdx.x & 31;
   const int64_t g = blockIdx.x * 4LL + wl;
   if (g >= (int64_t)nblk * n_fac) return;
   const int f = (int)(g / nblk), blk = (int)(g % nblk);
-  const double* LB = LBall + f * fstride;
-  double* B = Binv_all + ((int64_t)f * nblk + blk) * kBlk * kBlk;
+  const T* LB = LBall + f * fstride;
+  T* B = Binv_all + ((int64_t)f * nblk + blk) * kBlk * kBlk;
   const int i0 = blk * kBlk, W = bw + 1;
   for (int r = 0; r < kBlk; ++r) {
-    double x = (r == c) ? 1.0 : 0.0;
+    T x = (r == c) ? T(1) : T(0);
     const int i = i0 + r;
     if (i < n) {
       for (int j = 0; j < r; ++j)
@@ -175,31 +180,32 @@ struct Shape {
   static_assert(DW >= 2 && DW <= kBlk, "2 to 32 warps");
 };
 
+template <typename T>
 struct SolveSmem {
-  double part[2][kBlk][kBlk + 1];   // [buffer][row][lane] partial sums
-  double off[2][kBlk][kBlk + 1];    // [buffer][row][col] coupling block
-  double sacc[kBlk];
+  T part[2][kBlk][kBlk + 1];   // [buffer][row][lane] partial sums
+  T off[2][kBlk][kBlk + 1];    // [buffer][row][col] coupling block
+  T sacc[kBlk];
   double red[32];
 };
 
 // L~ y = w in place (w already scaled by D^-1, permuted order).
-template <int NT>
-__device__ void forward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
-                              int n, int bw, double* w, SolveSmem& sm) {
+template <int NT, typename T>
+__device__ void forward_subst(const T* __restrict__ LB, const T* __restrict__ Binv,
+                              int n, int bw, T* w, SolveSmem<T>& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kBlk - 1) / kBlk;
   // block 0 has no solved columns: empty partial sums and coupling
   for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += NT) {
-    (&sm.part[0][0][0])[t] = 0.0;
-    (&sm.off[0][0][0])[t] = 0.0;
+    (&sm.part[0][0][0])[t] = T(0);
+    (&sm.off[0][0][0])[t] = T(0);
   }
   __syncthreads();
   for (int b = 0; b < nblk; ++b) {
     const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
     if (warp == Shape<NT>::TRI) {
       const int i = i0 + lane;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {
         s0 += sm.part[cur][lane][q];
@@ -216,10 +222,10 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
           s3 = fma(sm.off[cur][lane][c + 3], w[i0 - kBlk + c + 3], s3);
         }
       }
-      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
+      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : T(0);
       __syncwarp();
-      const double* B = Binv + (int64_t)b * kBlk * kBlk + lane * kBlk;   // row `lane`
-      double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+      const T* B = Binv + (int64_t)b * kBlk * kBlk + lane * kBlk;   // row `lane`
+      T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
 #pragma unroll
       for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
         y0 = fma(B[c], sm.sacc[c], y0);
@@ -233,13 +239,13 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
       const int j0 = i0 + kBlk;
       for (int r = warp; r < kBlk; r += Shape<NT>::GW) {
         const int i = j0 + r;
-        double acc = 0.0;
+        T acc = T(0);
         if (i < n) {
-          const double* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L~(i, c)
+          const T* Lr = LB + (int64_t)i * W + (bw - i);   // Lr[c] = L~(i, c)
           int c = max(0, i - bw) + lane;
           for (; c + 96 < i0; c += 128) {
-            const double l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
-            const double w0 = w[c], w1 = w[c + 32], w2 = w[c + 64], w3 = w[c + 96];
+            const T l0 = Lr[c], l1 = Lr[c + 32], l2 = Lr[c + 64], l3 = Lr[c + 96];
+            const T w0 = w[c], w1 = w[c + 32], w2 = w[c + 64], w3 = w[c + 96];
             acc = fma(l0, w0, acc);
             acc = fma(l1, w1, acc);
             acc = fma(l2, w2, acc);
@@ -248,9 +254,9 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
           for (; c < i0; c += 32) acc = fma(Lr[c], w[c], acc);
           // coupling L~(i, i0 + lane) to block b, inside the band
           const int col = i0 + lane;
-          sm.off[nxt][r][lane] = (i - col <= bw) ? Lr[col] : 0.0;
+          sm.off[nxt][r][lane] = (i - col <= bw) ? Lr[col] : T(0);
         } else {
-          sm.off[nxt][r][lane] = 0.0;
+          sm.off[nxt][r][lane] = T(0);
         }
         sm.part[nxt][r][lane] = acc;
       }
@@ -260,22 +266,22 @@ __device__ void forward_subst(const double* __restrict__ LB, const double* __res
 }
 
 // L~^T u = w in place, from the last block up.
-template <int NT>
-__device__ void backward_subst(const double* __restrict__ LB, const double* __restrict__ Binv,
-                               int n, int bw, double* w, SolveSmem& sm) {
+template <int NT, typename T>
+__device__ void backward_subst(const T* __restrict__ LB, const T* __restrict__ Binv,
+                               int n, int bw, T* w, SolveSmem<T>& sm) {
   const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (n + kBlk - 1) / kBlk;
   for (int t = threadIdx.x; t < kBlk * (kBlk + 1); t += NT) {
-    (&sm.part[(nblk - 1) & 1][0][0])[t] = 0.0;
-    (&sm.off[(nblk - 1) & 1][0][0])[t] = 0.0;
+    (&sm.part[(nblk - 1) & 1][0][0])[t] = T(0);
+    (&sm.off[(nblk - 1) & 1][0][0])[t] = T(0);
   }
   __syncthreads();
   for (int b = nblk - 1; b >= 0; --b) {
     const int i0 = b * kBlk, cur = b & 1, nxt = cur ^ 1;
     if (warp == Shape<NT>::TRI) {
       const int i = i0 + lane;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {        // part[cur][q][col]: q = GEMV slot
         s0 += sm.part[cur][q][lane];
@@ -294,11 +300,11 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
           if (c + 3 < cm) s3 = fma(sm.off[cur][c + 3][lane], w[kb + c + 3], s3);
         }
       }
-      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : 0.0;
+      sm.sacc[lane] = i < n ? w[i] - ((s0 + s1) + (s2 + s3)) : T(0);
       __syncwarp();
       // u = (L~_blk^-1)^T acc: column `lane` of the inverted block
-      const double* B = Binv + (int64_t)b * kBlk * kBlk + lane;
-      double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+      const T* B = Binv + (int64_t)b * kBlk * kBlk + lane;
+      T u0 = T(0), u1 = T(0), u2 = T(0), u3 = T(0);
 #pragma unroll
       for (int c = 0; c < kBlk; c += 4) {       // B is zero above the diagonal
         u0 = fma(B[c * kBlk], sm.sacc[c], u0);
@@ -312,14 +318,14 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
       // k in [i0 + 32, j0 + 31 + bw]
       const int j0 = i0 - kBlk;
       const int col = j0 + lane;
-      double acc = 0.0;
+      T acc = T(0);
       const int kend = min(n - 1, j0 + kBlk - 1 + bw);
       int k = i0 + kBlk + warp;
       for (; k + 3 * Shape<NT>::GW <= kend && k + 3 * Shape<NT>::GW - j0 <= bw; k += 4 * Shape<NT>::GW) {
-        const double* r0 = LB + (int64_t)k * W + (col - k + bw);
-        const double l0 = r0[0], l1 = r0[Shape<NT>::GW * (W - 1)], l2 = r0[2 * Shape<NT>::GW * (W - 1)],
+        const T* r0 = LB + (int64_t)k * W + (col - k + bw);
+        const T l0 = r0[0], l1 = r0[Shape<NT>::GW * (W - 1)], l2 = r0[2 * Shape<NT>::GW * (W - 1)],
                      l3 = r0[3 * Shape<NT>::GW * (W - 1)];
-        const double w0 = w[k], w1 = w[k + Shape<NT>::GW], w2 = w[k + 2 * Shape<NT>::GW],
+        const T w0 = w[k], w1 = w[k + Shape<NT>::GW], w2 = w[k + 2 * Shape<NT>::GW],
                      w3 = w[k + 3 * Shape<NT>::GW];
         acc = fma(l0, w0, acc);
         acc = fma(l1, w1, acc);
@@ -332,11 +338,11 @@ __device__ void backward_subst(const double* __restrict__ LB, const double* __re
       }
       sm.part[nxt][warp][lane] = acc;
       if (warp == 0)   // slots without a partial-sum warp
-        for (int q = Shape<NT>::GW; q < kBlk; ++q) sm.part[nxt][q][lane] = 0.0;
+        for (int q = Shape<NT>::GW; q < kBlk; ++q) sm.part[nxt][q][lane] = T(0);
       // coupling rows i0 + r (block b) x column j0 + lane (block b-1)
       for (int r = warp; r < kBlk; r += Shape<NT>::GW) {
         const int kk = i0 + r;
-        sm.off[nxt][r][lane] = (kk < n && kk - col <= bw) ? LB[(int64_t)kk * W + (col - kk + bw)] : 0.0;
+        sm.off[nxt][r][lane] = (kk < n && kk - col <= bw) ? LB[(int64_t)kk * W + (col - kk + bw)] : T(0);
       }
     }
     __syncthreads();
@@ -361,13 +367,13 @@ struct DLaneOut {
 // On return the final state is in a0 (as given).
 template <int NT>
 __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int n_steps,
-                                 int64_t k0, SolveSmem& sm, DLaneOut& out) {
+                                 int64_t k0, SolveSmem<double>& sm, DLaneOut& out) {
   const int n = kc.n;
   double* a0 = D.a0;
   double* a1 = D.a1;
   double* y = D.y;
-  extern __shared__ double w_smem[];
-  double* w = kc.w_in_smem ? w_smem : D.w;
+  extern __shared__ unsigned char dyn_smem[];
+  double* w = kc.w_in_smem ? reinterpret_cast<double*>(dyn_smem) : D.w;
   const double* Mv = kc.M + D.vcol;
   const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
   if (D.init_from_a0) {
@@ -401,8 +407,8 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
       w[pi] = (y[i] / dt + f) * D.invd[pi];          // D^-1 b
     }
     __syncthreads();
-    forward_subst<NT>(D.LB, D.Binv, n, kc.bw, w, sm);
-    backward_subst<NT>(D.LB, D.Binv, n, kc.bw, w, sm);
+    forward_subst<NT, double>(D.LB, D.Binv, n, kc.bw, w, sm);
+    backward_subst<NT, double>(D.LB, D.Binv, n, kc.bw, w, sm);
     for (int i = threadIdx.x; i < n; i += NT) {
       const int pi = __ldg(kc.iperm + i);
       a1[i] = w[pi] * D.invd[pi];                     // x = D^-1 u
@@ -432,22 +438,141 @@ __device__ void direct_integrate(const DirectConst& kc, const DirectLane& D, int
   out.qoi = qacc;
 }
 
+// Mixed precision: FP32 band factor and FP32 substitutions, refined in FP64.
+// Each step starts from x = a_k; every sweep forms the FP64 residual
+// r = b - A x with the sample's FP64 matrix values, solves L L^T d = r with
+// the FP32 factor and adds d to x in FP64, until ||r|| <= tol ||b|| or the
+// sweep limit (status MQS_ST_NOTCONV).
 template <int NT>
+__device__ void direct_integrate_mixed(const DirectConst& kc, const DirectLane& D, int n_steps,
+                                       int64_t k0, SolveSmem<float>& sm, DLaneOut& out) {
+  const int n = kc.n;
+  double* a0 = D.a0;
+  double* a1 = D.a1;
+  double* y = D.y;
+  double* bvec = D.b;
+  extern __shared__ unsigned char dyn_smem[];
+  float* w = kc.w_in_smem ? reinterpret_cast<float*>(dyn_smem) : reinterpret_cast<float*>(D.w);
+  const double* Mv = kc.M + D.vcol;
+  const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
+  const double* Av = D.Av;
+  if (D.init_from_a0) {
+    for (int i = threadIdx.x; i < n; i += NT) y[i] = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a0);
+  } else {
+    for (int i = threadIdx.x; i < n; i += NT) {
+      a0[i] = 0.0;
+      y[i] = 0.0;
+    }
+  }
+  __syncthreads();
+  double qacc = 0.0;
+  int status = 0;
+  const double dt = D.dt;
+  for (int step = 0; step < n_steps; ++step) {
+    const double t = D.t0 + (double)(k0 + step + 1) * dt;
+    double g[kMaxPhases];
+#pragma unroll
+    for (int ph = 0; ph < kMaxPhases; ++ph) {
+      g[ph] = 0.0;
+      if (ph < kc.n_phases) {
+        const double arg = kc.omega * t - (2.0 * kPi * ph) / kc.n_phases + D.phase[ph];
+        g[ph] = D.amp[ph] * sin(arg);
+      }
+    }
+    double bb = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      double f = 0.0;
+#pragma unroll
+      for (int ph = 0; ph < kMaxPhases; ++ph)
+        if (ph < kc.n_phases) f = fma(g[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
+      const double bi = y[i] / dt + f;
+      bvec[i] = bi;
+      a1[i] = a0[i];
+      bb = fma(bi, bi, bb);
+    }
+    bb = block_sum<NT>(bb, sm.red);
+    for (int sweep = 0;; ++sweep) {
+      double rr = 0.0;
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const double ri = bvec[i] - csr_row(kc.rowptr, kc.colidx, i, Av, kc.vs, a1);
+        rr = fma(ri, ri, rr);
+        const int pi = __ldg(kc.iperm + i);
+        w[pi] = (float)ri * D.invdf[pi];               // D^-1 r in FP32
+      }
+      rr = block_sum<NT>(rr, sm.red);                   // also orders the w writes
+      if (rr <= kc.tol2 * bb) break;
+      if (sweep >= kc.max_sweeps || !isfinite(rr)) {
+        status |= isfinite(rr) ? MQS_ST_NOTCONV : MQS_ST_NONFINITE;
+        break;
+      }
+      forward_subst<NT, float>(D.LBf, D.Binvf, n, kc.bw, w, sm);
+      backward_subst<NT, float>(D.LBf, D.Binvf, n, kc.bw, w, sm);
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const int pi = __ldg(kc.iperm + i);
+        a1[i] += (double)(w[pi] * D.invdf[pi]);        // x += D^-1 u
+      }
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const double yn = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a1);
+      if (kc.qoi_kind == MQS_QOI_JOULE) {
+        part = fma(a1[i] - a0[i], yn - y[i], part);
+      } else {
+        part = fma(a1[i], csr_row(kc.rowptr, kc.colidx, i, Kv, kc.vs, a1), part);
+      }
+      y[i] = yn;
+    }
+    const double red = block_sum<NT>(part, sm.red);
+    qacc += kc.qoi_kind == MQS_QOI_JOULE ? red / dt : 0.5 * red;
+    double* tmp = a0;
+    a0 = a1;
+    a1 = tmp;
+    __syncthreads();
+  }
+  if (n_steps & 1) {
+    for (int i = threadIdx.x; i < n; i += NT) a1[i] = a0[i];
+    __syncthreads();
+  }
+  out.qoi = qacc;
+  if (threadIdx.x == 0 && status && D.status_out) *D.status_out |= status;
+}
+
+template <int NT, int PREC>
+struct Integrator;
+template <int NT>
+struct Integrator<NT, 0> {
+  using Smem = SolveSmem<double>;
+  __device__ static void run(const DirectConst& kc, const DirectLane& D, int n_steps, int64_t k0,
+                             Smem& sm, DLaneOut& out) {
+    direct_integrate<NT>(kc, D, n_steps, k0, sm, out);
+  }
+};
+template <int NT>
+struct Integrator<NT, 1> {
+  using Smem = SolveSmem<float>;
+  __device__ static void run(const DirectConst& kc, const DirectLane& D, int n_steps, int64_t k0,
+                             Smem& sm, DLaneOut& out) {
+    direct_integrate_mixed<NT>(kc, D, n_steps, k0, sm, out);
+  }
+};
+
+template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_propagate(const DirectLane* __restrict__ lanes,
-                                                         DirectConst kc) {
-  __shared__ SolveSmem sm;
+                                                                 DirectConst kc) {
+  __shared__ typename Integrator<NT, PREC>::Smem sm;
   const DirectLane D = lanes[blockIdx.x];
   DLaneOut out;
-  direct_integrate<NT>(kc, D, D.n_steps, D.k0, sm, out);
+  Integrator<NT, PREC>::run(kc, D, D.n_steps, D.k0, sm, out);
   if (threadIdx.x == 0) D.qoi_out[0] = out.qoi;
 }
 
 // Parareal coarse sweep, one CTA per sample; slice states lane-major
 // U/E/G[(sample*M + s) * n + i].
-template <int NT>
+template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_chain(const DirectLane* __restrict__ lanes,
-                                                     DirectConst kc, DirectChain ch) {
-  __shared__ SolveSmem sm;
+                                                             DirectConst kc, DirectChain ch) {
+  __shared__ typename Integrator<NT, PREC>::Smem sm;
   DirectLane D = lanes[blockIdx.x];
   const int n = kc.n;
   const int sample = D.sample;
@@ -457,7 +582,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_chain(const DirectLane
     for (int i = threadIdx.x; i < n; i += NT) D.a0[i] = ch.U[base + i];
     __syncthreads();
     DLaneOut out;
-    direct_integrate<NT>(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
+    Integrator<NT, PREC>::run(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
     double j2 = 0.0, u2 = 0.0;
     for (int i = threadIdx.x; i < n; i += NT) {
       const double gn = D.a0[i];
@@ -484,7 +609,10 @@ int block_count(int n) { return (n + kBlk - 1) / kBlk; }
 
 // Largest n whose work vector fits next to the static shared memory of the
 // stepping kernels (227 KB per CTA on sm_103).
-int direct_smem_max_n() { return (int)((227 * 1024 - (int)sizeof(SolveSmem) - 1024) / sizeof(double)); }
+int direct_smem_max_n(int mixed) {
+  const size_t fixed = mixed ? sizeof(SolveSmem<float>) : sizeof(SolveSmem<double>);
+  return (int)((227 * 1024 - fixed - 1024) / (mixed ? sizeof(float) : sizeof(double)));
+}
 
 namespace {
 
@@ -495,36 +623,41 @@ int grid_of(int64_t total, int block) {
 
 }  // namespace
 
-int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
-                double* invd, double* Binv, int32_t* bad, cudaStream_t st) {
+template <typename T>
+int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, T* LB, T* invd, T* Binv,
+                int32_t* bad, cudaStream_t st) {
   const int bw = m.bw;
   const int64_t fstride = (int64_t)m.n_free * (bw + 1);
-  MQS_CUDA_TRY(cudaMemsetAsync(LB, 0, (size_t)fstride * n_fac * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(LB, 0, (size_t)fstride * n_fac * sizeof(T), st));
   MQS_CUDA_TRY(cudaMemsetAsync(bad, 0, (size_t)n_fac * sizeof(int32_t), st));
-  k_band_fill<<<grid_of(m.nnz * n_fac, 256), 256, 0, st>>>(m.nnz, m.band_idx.as<int32_t>(), A, vs,
-                                                         n_fac, fstride, LB);
+  k_band_fill<T><<<grid_of(m.nnz * n_fac, 256), 256, 0, st>>>(m.nnz, m.band_idx.as<int32_t>(), A,
+                                                            vs, n_fac, fstride, LB);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
-  const size_t smem = (size_t)std::max(bw, 1) * sizeof(double);
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = (size_t)std::max(bw, 1) * sizeof(T);
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-  k_band_chol<<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
+  k_band_chol<T><<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
-  k_band_unit<<<grid_of((int64_t)m.n_free * n_fac, 8), dim3(32, 8), 0, st>>>(LB, invd, m.n_free, bw,
-                                                                          fstride, n_fac);
+  k_band_unit<T><<<grid_of((int64_t)m.n_free * n_fac, 8), dim3(32, 8), 0, st>>>(LB, invd, m.n_free,
+                                                                             bw, fstride, n_fac);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   const int nblk = (m.n_free + kBlk - 1) / kBlk;
-  k_block_inv<<<(unsigned)(((int64_t)nblk * n_fac + 3) / 4), 128, 0, st>>>(LB, Binv, m.n_free, bw,
-                                                                         fstride, nblk, n_fac);
+  k_block_inv<T><<<(unsigned)(((int64_t)nblk * n_fac + 3) / 4), 128, 0, st>>>(
+      LB, Binv, m.n_free, bw, fstride, nblk, n_fac);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
 }
+template int band_factor<double>(const MeshDev&, const double*, int64_t, int, double*, double*,
+                                 double*, int32_t*, cudaStream_t);
+template int band_factor<float>(const MeshDev&, const double*, int64_t, int, float*, float*,
+                                float*, int32_t*, cudaStream_t);
 
 size_t direct_smem(const DirectConst& kc) {
-  return kc.w_in_smem ? (size_t)kc.n * sizeof(double) : 0;
+  return kc.w_in_smem ? (size_t)kc.n * (kc.mixed ? sizeof(float) : sizeof(double)) : 0;
 }
 
 // Threads per lane-CTA: 1024 with the work vector in shared memory (one lane
@@ -532,25 +665,25 @@ size_t direct_smem(const DirectConst& kc) {
 // for large batches, so that several lanes per SM overlap their latencies.
 int direct_threads(const DirectConst& kc) { return kc.w_in_smem ? 1024 : 256; }
 
-template <int NT>
+template <int NT, int PREC>
 int launch_direct_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                     cudaStream_t st) {
   const size_t smem = direct_smem(kc);   // on top of the static SolveSmem
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate<NT>,
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_propagate<NT, PREC>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_direct_propagate<NT><<<n_lanes, NT, smem, st>>>(d_lanes, kc);
+  k_direct_propagate<NT, PREC><<<n_lanes, NT, smem, st>>>(d_lanes, kc);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
 }
 
-template <int NT>
+template <int NT, int PREC>
 int launch_chain_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                    const DirectChain& ch, cudaStream_t st) {
   const size_t smem = direct_smem(kc);
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain<NT>,
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_direct_chain<NT, PREC>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_direct_chain<NT><<<n_lanes, NT, smem, st>>>(d_lanes, kc, ch);
+  k_direct_chain<NT, PREC><<<n_lanes, NT, smem, st>>>(d_lanes, kc, ch);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;
@@ -558,15 +691,21 @@ int launch_chain_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc
 
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  return direct_threads(kc) == 1024 ? launch_direct_t<1024>(d_lanes, n_lanes, kc, st)
-                                    : launch_direct_t<256>(d_lanes, n_lanes, kc, st);
+  if (kc.mixed)
+    return direct_threads(kc) == 1024 ? launch_direct_t<1024, 1>(d_lanes, n_lanes, kc, st)
+                                      : launch_direct_t<256, 1>(d_lanes, n_lanes, kc, st);
+  return direct_threads(kc) == 1024 ? launch_direct_t<1024, 0>(d_lanes, n_lanes, kc, st)
+                                    : launch_direct_t<256, 0>(d_lanes, n_lanes, kc, st);
 }
 
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  return direct_threads(kc) == 1024 ? launch_chain_t<1024>(d_lanes, n_lanes, kc, ch, st)
-                                    : launch_chain_t<256>(d_lanes, n_lanes, kc, ch, st);
+  if (kc.mixed)
+    return direct_threads(kc) == 1024 ? launch_chain_t<1024, 1>(d_lanes, n_lanes, kc, ch, st)
+                                      : launch_chain_t<256, 1>(d_lanes, n_lanes, kc, ch, st);
+  return direct_threads(kc) == 1024 ? launch_chain_t<1024, 0>(d_lanes, n_lanes, kc, ch, st)
+                                    : launch_chain_t<256, 0>(d_lanes, n_lanes, kc, ch, st);
 }
 
 }  // namespace mqs

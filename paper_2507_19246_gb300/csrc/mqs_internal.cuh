@@ -158,6 +158,12 @@ struct DirectLane {
   const double* LB;        // this lane's band Cholesky factor [n][bw+1]
   const double* invd;      // its reciprocal diagonal [n]
   const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
+  const float* LBf;        // FP32 factor, reciprocal diagonal and block inverses (mixed)
+  const float* invdf;
+  const float* Binvf;
+  const double* Av;        // FP64 A values of this lane's sample and dt (mixed residual)
+  double* b;               // FP64 right-hand side [n] (mixed)
+  int32_t* status_out;     // MQS_ST_* bits of this lane (or-ed)
   double *a0, *a1, *y, *w; // lane vectors [n] (lane-major)
   double* qoi_out;         // raw QoI sum of the run
   int64_t vcol;            // value column (sample) of M / K values
@@ -178,7 +184,10 @@ struct DirectConst {
   int32_t n, bw, n_phases, qoi_kind;
   double omega;
   int32_t w_in_smem;       // 1: the permuted work vector lives in shared memory
-  int32_t pad_;
+  int32_t mixed;           // 1: FP32 factor with FP64 refinement sweeps
+  double tol2;             // mixed: stop when ||b - A x||^2 <= tol2 ||b||^2
+  int32_t max_sweeps;      // mixed: refinement sweep limit per step
+  int32_t pad2_;
 };
 
 struct DirectChain {
@@ -188,11 +197,12 @@ struct DirectChain {
 };
 
 // mqs_direct.cu
-int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, double* LB,
-                double* invd, double* Binv, int32_t* bad, cudaStream_t st);
+template <typename T>
+int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, T* LB, T* invd, T* Binv,
+                int32_t* bad, cudaStream_t st);
 int block_count(int n);
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
-int direct_smem_max_n();
+int direct_smem_max_n(int mixed);
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st);
 

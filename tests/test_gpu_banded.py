@@ -124,11 +124,64 @@ def test_banded_parareal_K_equals_M_is_serial(ctx, mqs):
     assert q[0] == pytest.approx(q[1], rel=1e-14)
 
 
-def test_banded_rejects_mixed_precision(ctx, mqs):
+def test_banded_rejects_unknown_solver(ctx, mqs):
     mesh = meshes.unit_square(8)
     mid = ctx.upload_mesh(mesh)
     b = ctx.set_samples(mid, params.square_samples(2))
+    with pytest.raises(mqs.MQSError, match="unknown solver"):
+        ctx.set_solver(b, 7)
+
+
+@pytest.mark.parametrize("wide", ["1", "0"])
+def test_banded_mixed_precision_qoi(ctx, mqs, monkeypatch, wide):
+    """FP32 band factor with FP64 refinement: QoI within 1e-6 of the FP64 oracle."""
+    monkeypatch.setenv("MQS_DIRECT_WIDE", wide)
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(8, 2)
+    dt1, dt0 = configs.level_dt(1), configs.level_dt(0)
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
     ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
-    ctx.set_time(b, 0.0, 0.02, 50.0, mqs.MQS_QOI_JOULE)
-    with pytest.raises(mqs.MQSError, match="FP64"):
-        ctx.propagate(b, 0, 0.02 / 16, precision=mqs.MQS_MIXED)
+    ctx.set_time(b, 0.0, configs.PERIOD, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 1, dt1, dt_prev=dt0, precision=mqs.MQS_MIXED, cg_tol=1e-10, cg_max_iters=20)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    for s in range(p.shape[0]):
+        qf, af, _ = stepper.solve_sample(mesh, p[s], dt1, 128, stepper.QOI_JOULE)
+        qc, _, _ = stepper.solve_sample(mesh, p[s], dt0, 64, stepper.QOI_JOULE)
+        assert abs(q[s, 0] - qf) <= 1e-6 * abs(qf) and abs(q[s, 1] - qc) <= 1e-6 * abs(qc), s
+        assert _rel(a[s], af) <= 1e-8, s
+
+
+def test_banded_mixed_sweep_limit_is_reported(ctx, mqs):
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(2, 0)
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, configs.PERIOD, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 0, configs.level_dt(0), precision=mqs.MQS_MIXED, cg_tol=1e-15,
+                  cg_max_iters=1)
+    _, st = ctx.read_qoi(b)
+    assert (st & mqs.MQS_ST_NOTCONV).all()
+
+
+def test_banded_mixed_parareal(ctx, mqs):
+    mesh = meshes.annulus("5k")
+    p = params.annulus_nominal(1)
+    n_steps, M, cf, tol = 256, 16, 4, 1e-8
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+    K = ctx.propagate(b, 0, dt, n_slices=M, coarse_factor=cf, max_par_iters=M, par_tol=tol,
+                      precision=mqs.MQS_MIXED, cg_tol=1e-10, cg_max_iters=20)
+    q, st = ctx.read_qoi(b)
+    assert not st.any()
+    d = fem.Discretisation(mesh, p[0])
+    ref = parareal.parareal_sample(d, dt, n_steps, M, cf, tol, stepper.QOI_JOULE)
+    q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
+    assert abs(K - ref["iters"]) <= 1
+    assert abs(q[0, 0] - q_ref) <= 1e-6 * abs(q_ref)
