@@ -67,6 +67,14 @@ def workload(name):
                     params=[params.annulus_samples(n, l) for l, n in enumerate(c.n_per_level)],
                     t_end=c.periods * configs.PERIOD, qoi=c.qoi, cg_tol=1e-12,
                     n_steps=None, dt=configs.level_dt(0), n_slices=1, cf=1, par_tol=0.0)
+    if name == "mlmc20k_short":
+        # profiling case: the MLMC workload's mesh, inputs and launch shapes over
+        # one period with 608/152/38/16 samples (level 0 fills 4 CTAs per SM)
+        c = configs.MLMCAnnulus(periods=1, n_per_level=(608, 152, 38, 16))
+        return dict(name="mlmc_annulus20k_short", mesh=meshes.annulus("20k"), mlmc=c,
+                    params=[params.annulus_samples(n, l) for l, n in enumerate(c.n_per_level)],
+                    t_end=c.periods * configs.PERIOD, qoi=c.qoi, cg_tol=1e-12,
+                    n_steps=None, dt=configs.level_dt(0), n_slices=1, cf=1, par_tol=0.0)
     if name == "mcsquare":
         c = configs.MC_SQUARE
         return dict(name="mc_square16", mesh=meshes.unit_square(16),
@@ -442,11 +450,14 @@ def run_mlmc(args, wl):
         estimate()
     torch.cuda.synchronize()
     times, res = [], None
+    ctx.profile(True)
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
             t0 = time.perf_counter()
             res = estimate()
             times.append(time.perf_counter() - t0)
+    prof = ctx.profile_read()
+    ctx.profile(False)
     lv, est, rmse = res
     units = c.solve_steps() * n_free
     line = {"metric": "sample-DoF-steps/s", "value": units * len(times) / sum(times),
@@ -459,7 +470,8 @@ def run_mlmc(args, wl):
                        "solver": args.solver, "precision": args.precision,
                        "solve_steps": c.solve_steps()},
             "time_to_rmse_s": statistics.median(times), "estimate": est, "rmse": rmse,
-            "levels": lv.tolist(), "clocks": clk.summary()}
+            "levels": lv.tolist(), "clocks": clk.summary(),
+            "kernel_ms": {"stepping": prof[2] / len(times), "coarse_sweep": prof[4] / len(times)}}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -471,7 +483,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare", "mlmc20k"])
+    ap.add_argument("--workload", default="parareal20k", choices=["parareal20k", "parareal20k_short", "mcsquare", "mlmc20k",
+                             "mlmc20k_short"])
     ap.add_argument("--solver", default="banded", choices=["pcg", "banded"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -479,7 +492,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     dist = None
     wl = workload(args.workload)
-    if args.workload == "mlmc20k" and args.impl != "reference":
+    if args.workload.startswith("mlmc20k") and args.impl != "reference":
         run_mlmc(args, wl)
         return
     if args.impl == "reference":
