@@ -57,6 +57,8 @@ extern "C" {
 #define MQS_ST_NOTCONV 1  /* some step's linear solve stopped at the iteration limit */
 #define MQS_ST_NONFINITE 2 /* a residual norm became NaN or Inf */
 #define MQS_ST_NOTSPD  4  /* a band Cholesky factorisation met a non-positive pivot */
+#define MQS_ST_TIMEOUT 8  /* a wait between the CTAs of a cluster ran out of its iteration
+                             limit; the lane's results are invalid */
 
 typedef struct mqs_ctx mqs_ctx;
 

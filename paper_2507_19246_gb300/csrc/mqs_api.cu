@@ -41,8 +41,9 @@ struct ValueSet {
 
 struct FactorSet {
   double dt = 0.0;
-  bool have64 = false, have32 = false;
+  bool have64 = false, have32 = false, have_cpl = false;
   DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
+  DevBuf Cf, Db;                // [samples][n/32][32][32] block couplings (cluster kernels)
   DevBuf LBf, invdf, Binvf;     // FP32 factor (mixed precision)
 };
 
@@ -587,7 +588,33 @@ FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool 
                              ctx->c.stream);
     f->have64 = rc == MQS_OK;
   }
+  if (rc == MQS_OK && !mixed) f->have_cpl = false;   // new factor: couplings are stale
   return rc == MQS_OK ? f : nullptr;
+}
+
+// Block couplings of an FP64 factor set, for the cluster stepping kernels.
+int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
+  if (f.have_cpl) return MQS_OK;
+  const size_t bstride = (size_t)block_count(m.n_free) * 32 * 32;
+  MQS_TRY(f.Cf.ensure(bstride * b.n * sizeof(double)));
+  MQS_TRY(f.Db.ensure(bstride * b.n * sizeof(double)));
+  MQS_TRY(block_couplings(m, b.n, f.LB.as<double>(), f.Binv.as<double>(), f.Cf.as<double>(),
+                          f.Db.as<double>(), ctx->c.stream));
+  f.have_cpl = true;
+  return MQS_OK;
+}
+
+// Cluster size of the FP64 stepping kernels with the work vector in shared
+// memory: the widest split (8, 4, 2, 1 CTAs per lane) whose clusters are all
+// resident at once; 0 selects the one-CTA kernels (mixed precision, work
+// vector in L2).  env MQS_DIRECT_CLUSTER=0/1/2/4/8 forces a choice.
+int direct_cluster(const MeshDev& m, int lanes, const DirectConst& kc) {
+  if (kc.mixed || !kc.w_in_smem || m.n_free > cluster_max_n()) return 0;
+  const int forced = env_int("MQS_DIRECT_CLUSTER", -1);
+  if (forced == 0 || forced == 1 || forced == 2 || forced == 4 || forced == 8) return forced;
+  for (int cl : {8, 4, 2})
+    if (lanes <= cluster_max_active(cl, m.n_free)) return cl;
+  return 1;
 }
 
 // lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
@@ -599,6 +626,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, 
   kc.rowptr = m.rowptr.as<int32_t>();
   kc.colidx = m.colidx.as<int32_t>();
   kc.iperm = m.iperm.as<int32_t>();
+  kc.perm = m.perm.as<int32_t>();
   kc.M = b.Mv.as<double>();
   kc.K = b.qoi_kind == MQS_QOI_ENERGY ? b.Kv.as<double>() : nullptr;
   kc.vs = b.n;
@@ -614,6 +642,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, 
   kc.mixed = mixed ? 1 : 0;
   kc.tol2 = tol * tol;
   kc.max_sweeps = max_sweeps;
+  kc.cluster = direct_cluster(m, lanes, kc);
   return kc;
 }
 
@@ -627,6 +656,8 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   d.LB = f.LB.as<double>() + fstride * sample;
   d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
   d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  d.Cf = f.Cf.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  d.Db = f.Db.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
   d.LBf = f.LBf.as<float>() + fstride * sample;
   d.invdf = f.invdf.as<float>() + (size_t)m.n_free * sample;
   d.Binvf = f.Binvf.as<float>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
@@ -664,11 +695,16 @@ int upload_direct(mqs_ctx* ctx, DirectSet& ds) {
 }
 
 // Sequential stepping with the banded solver: lanes [0, nf) level l, [nf, nf+nc) level l-1.
-int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* ff, int nsf,
-                     const FactorSet* fc, int nsc, bool mixed, double tol, int max_sweeps) {
+int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet* ff, int nsf,
+                     FactorSet* fc, int nsc, bool mixed, double tol, int max_sweeps) {
   const int nf = ff ? b.n : 0, nc = fc ? b.n : 0;
   DirectSet& ds = b.dplain;
   MQS_TRY(ds.ensure(nf + nc, m.n_free));
+  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm, mixed, tol, max_sweeps);
+  if (kc.cluster) {
+    if (ff) MQS_TRY(ensure_couplings(ctx, b, m, *ff));
+    if (fc) MQS_TRY(ensure_couplings(ctx, b, m, *fc));
+  }
   MQS_CUDA_TRY(cudaMemsetAsync(ds.qraw.p, 0, (size_t)(nf + nc) * sizeof(double), ctx->c.stream));
   MQS_CUDA_TRY(cudaMemsetAsync(ds.status.p, 0, (size_t)(nf + nc) * sizeof(int32_t), ctx->c.stream));
   ds.host.clear();
@@ -684,9 +720,11 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* 
   }
   b.nf_direct = nf;
   MQS_TRY(upload_direct(ctx, ds));
-  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm, mixed, tol, max_sweeps);
   MQS_TRY(prof_mark(ctx->c, 0, true));
-  MQS_TRY(launch_direct(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
+  if (kc.cluster)
+    MQS_TRY(launch_cluster(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
+  else
+    MQS_TRY(launch_direct(ds.desc.as<DirectLane>(), nf + nc, kc, ctx->c.stream));
   MQS_TRY(prof_mark(ctx->c, 0, false));
   b.stats[1] += (double)nf * nsf + (double)nc * nsc;
   b.stats[2] += (double)nf * nsf + (double)nc * nsc;
@@ -694,8 +732,8 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet* 
   return MQS_OK;
 }
 
-int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSet& fF,
-                        const FactorSet& fC, int n_steps, int M, int cf, int max_iters, double tol,
+int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
+                        FactorSet& fC, int n_steps, int M, int cf, int max_iters, double tol,
                         bool mixed, double ir_tol, int max_sweeps, int& iters_out) {
   const cudaStream_t st = ctx->c.stream;
   const int S = n_steps / M, Sc = S / cf, ns = b.n, n = m.n_free;
@@ -716,6 +754,16 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
   MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
   const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
   const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
+  if (kc.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fF));
+  if (kchain.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fC));
+  auto fine = [&](const DirectSet& d, int nl) -> int {
+    return kc.cluster ? launch_cluster(d.desc.as<DirectLane>(), nl, kc, st)
+                      : launch_direct(d.desc.as<DirectLane>(), nl, kc, st);
+  };
+  auto chain = [&](const DirectChain& c) -> int {
+    return kchain.cluster ? launch_cluster_chain(b.dchain.desc.as<DirectLane>(), ns, kchain, c, st)
+                          : launch_direct_chain(b.dchain.desc.as<DirectLane>(), ns, kchain, c, st);
+  };
   DirectSet& dc = b.dchain;
   dc.host.clear();
   for (int s = 0; s < ns; ++s)
@@ -735,7 +783,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
   ch.first_sweep = 1;
   MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_TRY(prof_mark(ctx->c, 1, true));
-  MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kchain, ch, st));
+  MQS_TRY(chain(ch));
   MQS_TRY(prof_mark(ctx->c, 1, false));
   double exec_steps = (double)ns * (M - 1) * Sc, chain_steps = exec_steps, fine_steps = 0.0;
   std::vector<double> hj((size_t)lanes), hn((size_t)lanes);
@@ -756,14 +804,14 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, const FactorSe
     exec_steps += (double)dp.host.size() * S;
     MQS_TRY(upload_direct(ctx, dp));
     MQS_TRY(prof_mark(ctx->c, 0, true));
-    MQS_TRY(launch_direct(dp.desc.as<DirectLane>(), (int)dp.host.size(), kc, st));
+    MQS_TRY(fine(dp, (int)dp.host.size()));
     MQS_TRY(prof_mark(ctx->c, 0, false));
     MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
     if (k - 1 <= M - 2) {
       ch.s_begin = k - 1;
       ch.first_sweep = 0;
       MQS_TRY(prof_mark(ctx->c, 1, true));
-      MQS_TRY(launch_direct_chain(dc.desc.as<DirectLane>(), ns, kchain, ch, st));
+      MQS_TRY(chain(ch));
       MQS_TRY(prof_mark(ctx->c, 1, false));
       exec_steps += (double)ns * (M - 1 - (k - 1)) * Sc;
       chain_steps += (double)ns * (M - 1 - (k - 1)) * Sc;

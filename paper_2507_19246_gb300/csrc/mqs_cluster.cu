@@ -1,0 +1,792 @@
+// Banded direct solver, FP64 stepping kernels with the block substitution
+// spread over warps and, optionally, over the CTAs of a thread-block cluster
+// (Sec. II-A, Eq. 7: one factorisation per (sample, dt), one forward and one
+// backward substitution per implicit-Euler step).
+//
+// FP64 on this GPU retires one warp instruction per 64 cycles on each of the
+// four SM sub-partitions, whatever the number of active lanes, and a dependent
+// FP64 instruction waits as long.  The substitution is therefore organised so
+// that (1) the dense work of every 32-row block runs on four warps (one per
+// sub-partition) instead of one, (2) the band products (GEMV) run on other
+// warps with long per-lane FMA chains and few reduction levels, and (3) one
+// lane may be split over a cluster of CL CTAs on CL SMs.
+//
+// Algebra (unit lower factor L~ = D^-1 L, 32-row blocks, B_b = L~_bb^-1):
+//   forward  L~ y = w:    y_b = B_b (w_b - P_b) - C_b y_{b-1},
+//                         C_b = B_b L~_{b,b-1},   P_b = sum_{k <= b-2} L~_bk y_k
+//   backward L~^T u = y:  u_b = B_b^T (y_b - Q_b) - D_b u_{b+1},
+//                         D_b = B_b^T L~_{b+1,b}^T, Q_b = sum_{k >= b+2} L~_kb^T u_k
+// C_b and D_b^T = L~_{b+1,b} B_b are precomputed with the factor.  P and Q
+// of block b are computed while block b-1 (b+1) is being solved.
+//
+// Cluster split: every CTA keeps a full copy of the permuted work vector in
+// shared memory and owns rows q*R .. q*R+R-1 (R = 32/CL) of every block, in
+// the band ordering.  Per block it computes P (Q) for its own rows and its
+// share of the block solve, v_q = B_b[:, own] s_b[own] - C_b[:, own] y_{b-1}[own],
+// which it sends to every CTA of the cluster with asynchronous DSMEM stores
+// that complete on the receiver's mbarrier (no fence on the sending side, no
+// cluster barrier per block); each CTA adds the CL shares in rank order, so
+// all copies hold identical values.  Waits are bounded: a wait that runs out
+// sets MQS_ST_TIMEOUT on the lane and the kernel skips every later wait.
+// Node-wise work (right-hand side, y = M a, QoI) is split by the same row
+// ownership, so a step exchanges no data through global memory except the new
+// state a1, which is published by a cluster barrier before y = M a1.
+#include "mqs_internal.cuh"
+
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace mqs {
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int kB = 32;       // rows per substitution block
+constexpr int kNT = 512;     // threads per CTA
+constexpr int kNW = kNT / 32;
+constexpr int kSW = 4;       // solve warps (warps 0..3, one per SM sub-partition)
+constexpr int kPF = 24;      // band values prefetched per GEMV lane (registers)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWaitLimit = 1 << 20;   // mbarrier polls before a wait gives up
+// bytes of block-solve shares a CTA receives from the other CTAs per round
+template <int CL>
+constexpr uint32_t kShareTx = (CL - 1) * kB * sizeof(double);
+constexpr double kPi = 3.14159265358979323846;
+
+template <int CL>
+struct Split {
+  static constexpr int R = kB / CL;              // own rows per block
+  static constexpr int GW = CL <= 2 ? 8 : 4;     // GEMV warps (warps kSW .. kSW+GW-1)
+  static constexpr int H = 4 * GW / R;           // forward: chunks per own row, 8 lanes each
+  static constexpr int TB = R / GW;              // backward: own columns per GEMV warp
+  static constexpr int KG = 32 / TB;             // backward: row groups per own column
+  static constexpr int TPL = (R + 3) / 4;        // own rows per solve lane
+  static_assert(R * H == 4 * GW && H <= 4, "forward items fill the GEMV warps, rows stay in a warp");
+  static_assert(TB >= 1 && TB * GW == R, "backward columns fill the GEMV warps");
+  static_assert(kSW + GW <= kNW, "warp roles");
+  static_assert(2 * TPL <= kPF, "solve prefetch fits the register array");
+};
+
+template <int CL>
+struct CSmem {
+  double V[2][CL][kB];                       // block-solve shares [round parity][rank][row]
+  double s[2][Split<CL>::R];                 // own rows' right-hand side of the block solve
+  unsigned long long mbar[2];                // share arrivals of V[0], V[1]
+  int err;                                   // a wait ran out
+  double red[kNW];
+  double cred[CL][2];                        // per-rank partial sums for cluster reductions
+};
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// 8-byte store into another CTA's shared memory that completes (bytes) on
+// that CTA's mbarrier.
+__device__ __forceinline__ void st_async(uint32_t raddr, double v, uint32_t rmbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
+               :: "r"(raddr), "d"(v), "r"(rmbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar) : "memory");
+}
+
+// The single arrival of a phase, announcing tx bytes.
+__device__ __forceinline__ void mbar_arm(uint32_t mbar, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(tx)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity, at most kWaitLimit polls; after a
+// failed wait every later wait of the CTA returns at once.
+__device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t parity, int* err) {
+  if (*reinterpret_cast<volatile int*>(err)) return;
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(mbar, parity)) return;
+  *reinterpret_cast<volatile int*>(err) = 1;
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Deterministic CTA-wide sum (warp butterfly, then warps in order).
+__device__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int j = 0; j < kNW; ++j) s += red[j];
+  return s;
+}
+
+// Sum of a per-CTA value over the cluster, in rank order (identical on every
+// rank).  slot selects one of two independent sums.
+template <int CL>
+__device__ double cluster_sum(double v, CSmem<CL>& sm, int slot, unsigned q) {
+  if constexpr (CL == 1) {
+    return v;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x < CL) *cl.map_shared_rank(&sm.cred[q][slot], threadIdx.x) = v;
+    cluster_sync_all();
+    double s = 0.0;
+    for (int p = 0; p < CL; ++p) s += sm.cred[p][slot];
+    cluster_sync_all();   // slots free for the next use
+    return s;
+  }
+}
+
+__device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr,
+                                          const int32_t* __restrict__ colidx, int i,
+                                          const double* __restrict__ vals, int64_t vs,
+                                          const double* x) {
+  double acc = 0.0;
+  for (int k = __ldg(rowptr + i); k < __ldg(rowptr + i + 1); ++k)
+    acc = fma(__ldg(vals + (int64_t)k * vs), x[__ldg(colidx + k)], acc);
+  return acc;
+}
+
+// One GEMV work item of a lane: cnt band values at LB[off + j*step], each
+// multiplied by w[w0 + j*wstep].
+struct GemvDesc {
+  int64_t off, step;
+  int cnt, w0, wstep;
+};
+
+// ---------------------------------------------------------------- substitution
+template <int CL>
+struct Subst {
+  using S = Split<CL>;
+  const double* __restrict__ LB;
+  const double* __restrict__ Binv;
+  const double* __restrict__ Cf;
+  const double* __restrict__ Db;
+  double* w;
+  CSmem<CL>& sm;
+  int n, bw, W, nblk, q;
+  // lane roles
+  int warp, lane;
+  int f_t, f_h, f_g;     // forward GEMV item: own row, chunk, lane in chunk
+  int b_t, b_kg, gw;     // backward GEMV: own column, row group; GEMV warp index
+  int s_r, s_g;          // solve lane: block row, term group
+  int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
+
+  __device__ Subst(const double* LB_, const double* Binv_, const double* Cf_, const double* Db_,
+                   double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
+      : LB(LB_), Binv(Binv_), Cf(Cf_), Db(Db_), w(w_), sm(sm_), n(n_), bw(bw_), W(bw_ + 1),
+        nblk((n_ + kB - 1) / kB), q(q_) {
+    warp = threadIdx.x >> 5;
+    lane = threadIdx.x & 31;
+    gw = warp - kSW;
+    const int item = gw * 4 + (lane >> 3);
+    f_t = item / S::H;
+    f_h = item % S::H;
+    f_g = lane & 7;
+    b_t = gw * S::TB + lane % S::TB;
+    b_kg = lane / S::TB;
+    s_r = warp * 8 + (lane & 7);
+    s_g = lane >> 3;
+  }
+
+  __device__ bool is_solve() const { return warp < kSW; }
+  __device__ bool is_gemv() const { return warp >= kSW && warp < kSW + S::GW; }
+  __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
+
+  // GEMV of round g: the partial sums of the block solved in round g + 1,
+  // over the part of the band already known when round g starts.
+  __device__ GemvDesc gemv_desc(int g) const {
+    GemvDesc d{0, 0, 0, 0, 0};
+    const int g1 = g + 1;
+    if (g1 >= 2 * nblk) return d;
+    if (g1 < nblk) {   // forward: row i of block g1, columns of blocks <= g1 - 2
+      const int i = g1 * kB + q * S::R + f_t;
+      if (i >= n) return d;
+      const int lo = max(0, i - bw), hi = g * kB;
+      const int c0 = lo + 8 * f_h + f_g, st = 8 * S::H;
+      if (c0 >= hi) return d;
+      d.cnt = (hi - c0 + st - 1) / st;
+      d.off = (int64_t)i * W + (c0 - i + bw);
+      d.step = st;
+      d.w0 = c0;
+      d.wstep = st;
+    } else {           // backward: column c of block bt, rows of blocks >= bt + 2
+      const int bt = 2 * nblk - 1 - g1;
+      const int c = bt * kB + q * S::R + b_t;
+      if (c >= n) return d;
+      const int kend = min(n - 1, c + bw);
+      const int st = S::KG;
+      const int k0 = (bt + 2) * kB + b_kg;
+      if (k0 > kend) return d;
+      d.cnt = (kend - k0) / st + 1;
+      d.off = (int64_t)k0 * W + (c - k0 + bw);
+      d.step = (int64_t)st * bw;
+      d.w0 = k0;
+      d.wstep = st;
+    }
+    return d;
+  }
+
+  // Loads of one GEMV item into registers, stopping at the longest item of
+  // the warp (each load instruction costs issue time even when its lanes are off).
+  __device__ void gemv_load(const GemvDesc& d, double (&pf)[kPF]) const {
+    const int cmax = __reduce_max_sync(kFull, d.cnt);
+#pragma unroll
+    for (int j = 0; j < kPF; ++j) {
+      if (j >= cmax) break;
+      pf[j] = j < d.cnt ? __ldg(LB + d.off + j * d.step) : 0.0;
+    }
+  }
+
+  // Block-solve operands of round g for this solve lane: pf[2j] = B entry,
+  // pf[2j+1] = coupling entry, own row t = s_g + 4j.
+  __device__ void solve_load(int g, double (&pf)[kPF]) const {
+    if (g >= 2 * nblk) return;
+    const bool fwd = g < nblk;
+    const int b = block_of(g);
+    const double* Bb = Binv + (int64_t)b * kB * kB;
+#pragma unroll
+    for (int j = 0; j < S::TPL; ++j) {
+      const int t = s_g + 4 * j;
+      double bv = 0.0, cv = 0.0;
+      if (t < S::R) {
+        const int tc = q * S::R + t;
+        if (fwd) {
+          bv = __ldg(Bb + s_r * kB + tc);
+          if (b >= 1) cv = __ldg(Cf + (int64_t)b * kB * kB + s_r * kB + tc);
+        } else {
+          bv = __ldg(Bb + tc * kB + s_r);
+          if (b + 1 < nblk) cv = __ldg(Db + (int64_t)b * kB * kB + tc * kB + s_r);
+        }
+      }
+      pf[2 * j] = bv;
+      pf[2 * j + 1] = cv;
+    }
+  }
+
+  // GEMV of round g (see gemv_desc): completes the own rows' sums inside the
+  // warp and stores the right-hand side s of the block solved in round g + 1.
+  // The block after the last forward one takes its s in that round (phase A).
+  // Once the products are formed, the loads of round g + 1 are issued (into
+  // pf, cur) so that they overlap the reduction.
+  __device__ void gemv_round(int g, GemvDesc& cur, double (&pf)[kPF]) {
+    // every FP64 warp instruction costs the same however many lanes are
+    // active, so the loop stops at the longest item of the warp; two
+    // accumulators halve the dependent chain
+    const int cmax = __reduce_max_sync(kFull, cur.cnt);
+    double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < kPF; j += 2) {
+      if (j >= cmax) break;
+      const double x0 = j < cur.cnt ? w[cur.w0 + j * cur.wstep] : 0.0;
+      acc0 = fma(pf[j], x0, acc0);
+      if (j + 1 >= cmax) break;
+      const double x1 = j + 1 < cur.cnt ? w[cur.w0 + (j + 1) * cur.wstep] : 0.0;
+      acc1 = fma(pf[j + 1], x1, acc1);
+    }
+    for (int j = kPF; j < cmax; ++j)
+      if (j < cur.cnt) acc0 = fma(__ldg(LB + cur.off + j * cur.step), w[cur.w0 + j * cur.wstep], acc0);
+    cur = gemv_desc(g + 1);
+    gemv_load(cur, pf);
+    double acc = acc0 + acc1;
+    const int g1 = g + 1;
+    if (g1 >= 2 * nblk || g1 == nblk) return;
+    double* s_next = sm.s[g1 & 1];
+    if (g1 < nblk) {
+      acc += __shfl_xor_sync(kFull, acc, 1);
+      acc += __shfl_xor_sync(kFull, acc, 2);
+      acc += __shfl_xor_sync(kFull, acc, 4);
+      if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 8);
+      if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 16);
+      if (f_g == 0 && f_h == 0) {
+        const int row = g1 * kB + q * S::R + f_t;
+        s_next[f_t] = row < n ? w[row] - acc : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int o = S::TB; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      if (b_kg == 0) {
+        const int row = (2 * nblk - 1 - g1) * kB + q * S::R + b_t;
+        s_next[b_t] = row < n ? w[row] - acc : 0.0;
+      }
+    }
+  }
+
+  // Forward then backward substitution; on return w holds u (all rows).
+  __device__ void run(double (&pf)[kPF]) {
+    const int G = 2 * nblk;
+    GemvDesc cur{0, 0, 0, 0, 0};
+    if (is_gemv()) {
+      gemv_round(-1, cur, pf);   // block 0: s = own right-hand sides; loads of round 0
+    } else if (is_solve()) {
+      solve_load(0, pf);
+    }
+    __syncthreads();
+    const int rl = s_r - q * S::R;                  // own-row index of a solve lane
+    const bool own = is_solve() && rl >= 0 && rl < S::R;
+    for (int g = 0; g <= G; ++g) {
+      const bool fwd = g < nblk;
+      const int b = block_of(g);
+      // ---------------- phase A: gather the last block's shares into the copy
+      if ((CL > 1 && g >= 1) || g == nblk) {
+        if (is_solve()) {
+          double yv = 0.0;
+          if (CL > 1 && g >= 1) {
+            const int bp = block_of(g - 1);
+            const int64_t r = rounds + g - 1;   // round whose shares arrive
+            const uint32_t mb = smem_addr(&sm.mbar[r & 1]);
+            mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
+            if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
+            const double* Vb = &sm.V[(g - 1) & 1][0][0];
+            double acc = s_g < CL ? Vb[s_g * kB + s_r] : 0.0;
+            for (int p = s_g + 4; p < CL; p += 4) acc += Vb[p * kB + s_r];
+            if (CL > 1) acc += __shfl_xor_sync(kFull, acc, 8);
+            if (CL > 2) acc += __shfl_xor_sync(kFull, acc, 16);
+            yv = acc;
+            const int row = bp * kB + s_r;
+            if (s_g == 0 && row < n) w[row] = yv;
+          }
+          if (g == nblk && own && s_g == 0) {   // first backward block: s = y (Q = 0)
+            const int row = (nblk - 1) * kB + s_r;
+            sm.s[g & 1][rl] = row < n ? (CL > 1 ? yv : w[row]) : 0.0;
+          }
+        }
+        __syncthreads();
+      }
+      if (g == G) break;
+      // ---------------- phase B: block solve share, GEMV one block ahead
+      if (is_solve()) {
+        const double* sb = sm.s[g & 1];
+        double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::TPL; ++j) {
+          const int t = s_g + 4 * j;
+          if (t < S::R) {
+            double yo = 0.0;
+            if (fwd) {
+              if (b >= 1) yo = w[(b - 1) * kB + q * S::R + t];
+            } else {
+              const int row = (b + 1) * kB + q * S::R + t;
+              if (b + 1 < nblk && row < n) yo = w[row];
+            }
+            v0 = fma(pf[2 * j], sb[t], v0);
+            v1 = fma(-pf[2 * j + 1], yo, v1);
+          }
+        }
+        double v = v0 + v1;
+        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 8);
+        if (S::R > 2) v += __shfl_xor_sync(kFull, v, 16);
+        if constexpr (CL == 1) {
+          const int row = b * kB + s_r;
+          if (s_g == 0 && row < n) w[row] = v;
+        } else {
+          const uint32_t la = smem_addr(&sm.V[g & 1][q][s_r]);
+          const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
+          for (int p = s_g; p < CL; p += 4) {
+            if (p == q)
+              sm.V[g & 1][q][s_r] = v;   // own share: ordered by the CTA barrier below
+            else
+              st_async(map_rank(la, p), v, map_rank(lm, p));
+          }
+        }
+        solve_load(g + 1, pf);
+      } else if (is_gemv()) {
+        gemv_round(g, cur, pf);
+      }
+      __syncthreads();
+    }
+    rounds += G;
+  }
+};
+
+// ---------------------------------------------------------------- stepping
+// Own nodes of rank q: band rows pi with (pi mod 32) in [q*R, q*R + R).
+template <int CL>
+struct Own {
+  int n, q;
+  __device__ int count() const { return ((n + kB - 1) / kB) * Split<CL>::R; }
+  __device__ int row(int idx) const {
+    constexpr int R = Split<CL>::R;
+    return (idx / R) * kB + q * R + idx % R;
+  }
+};
+
+// mbarriers of the share exchange: initialised once, each armed one round
+// ahead (rounds 0 and 1 here, round r + 2 when round r's shares are consumed).
+template <int CL>
+__device__ void cluster_setup(CSmem<CL>& sm) {
+  if constexpr (CL > 1) {
+    if (threadIdx.x == 0) {
+      sm.err = 0;
+      for (int x = 0; x < 2; ++x) {
+        const uint32_t mb = smem_addr(&sm.mbar[x]);
+        mbar_init(mb);
+        mbar_arm(mb, kShareTx<CL>);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();
+  }
+}
+
+// No CTA leaves while shares may still be sent to it; a timed-out wait is
+// reported on the lane's status.
+template <int CL>
+__device__ void cluster_finish(CSmem<CL>& sm, const DirectLane& D) {
+  if constexpr (CL > 1) {
+    cluster_sync_all();
+    if (threadIdx.x == 0 && sm.err && D.status_out) atomicOr(D.status_out, MQS_ST_TIMEOUT);
+  }
+}
+
+// Advance one lane by n_steps steps.  a_init: initial state (all nodes
+// readable) or nullptr for zero; on return the final state is in D.a0 (own
+// nodes).  Returns this thread's share of the raw QoI sum when want_qoi.
+template <int CL>
+__device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
+                                    const double* a_init, int n_steps, int64_t k0, unsigned q,
+                                    Subst<CL>& sub, double* w, bool want_qoi) {
+  const int n = kc.n;
+  const Own<CL> own{n, (int)q};
+  const int n_own = own.count();
+  double* a0 = D.a0;
+  double* a1 = D.a1;
+  double* y = D.y;
+  const double* Mv = kc.M + D.vcol;
+  const double* Kv = kc.K ? kc.K + D.vcol : nullptr;
+  for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+    const int pi = own.row(idx);
+    if (pi >= n) continue;
+    const int i = __ldg(kc.perm + pi);
+    if (a_init) {
+      y[i] = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a_init);
+      if (a_init != a0) a0[i] = a_init[i];
+    } else {
+      a0[i] = 0.0;
+      y[i] = 0.0;
+    }
+  }
+  double pf[kPF];
+  double qacc = 0.0;
+  const double dt = D.dt, inv_dt = 1.0 / D.dt;
+  for (int step = 0; step < n_steps; ++step) {
+    const double t = D.t0 + (double)(k0 + step + 1) * dt;
+    double gph[kMaxPhases];
+#pragma unroll
+    for (int ph = 0; ph < kMaxPhases; ++ph) {
+      gph[ph] = 0.0;
+      if (ph < kc.n_phases) {
+        const double arg = kc.omega * t - (2.0 * kPi * ph) / kc.n_phases + D.phase[ph];
+        gph[ph] = D.amp[ph] * sin(arg);
+      }
+    }
+    for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+      const int pi = own.row(idx);
+      if (pi >= n) continue;
+      const int i = __ldg(kc.perm + pi);
+      double f = 0.0;
+#pragma unroll
+      for (int ph = 0; ph < kMaxPhases; ++ph)
+        if (ph < kc.n_phases) f = fma(gph[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
+      w[pi] = fma(y[i], inv_dt, f) * __ldg(D.invd + pi);     // D^-1 b, b = M a_k / dt + f
+    }
+    __syncthreads();
+    sub.run(pf);
+    for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+      const int pi = own.row(idx);
+      if (pi >= n) continue;
+      const int i = __ldg(kc.perm + pi);
+      a1[i] = w[pi] * __ldg(D.invd + pi);                    // x = D^-1 u
+    }
+    if constexpr (CL == 1) {                                  // a1 complete for y = M a1
+      __syncthreads();
+    } else {
+      cluster_sync_all();
+    }
+    for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+      const int pi = own.row(idx);
+      if (pi >= n) continue;
+      const int i = __ldg(kc.perm + pi);
+      const double yn = csr_row(kc.rowptr, kc.colidx, i, Mv, kc.vs, a1);
+      if (want_qoi) {
+        if (kc.qoi_kind == MQS_QOI_JOULE)
+          qacc = fma(a1[i] - a0[i], yn - y[i], qacc);
+        else
+          qacc = fma(a1[i], csr_row(kc.rowptr, kc.colidx, i, Kv, kc.vs, a1), qacc);
+      }
+      y[i] = yn;
+    }
+    double* tmp = a0;
+    a0 = a1;
+    a1 = tmp;
+  }
+  if (n_steps & 1) {
+    for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+      const int pi = own.row(idx);
+      if (pi >= n) continue;
+      const int i = __ldg(kc.perm + pi);
+      a1[i] = a0[i];
+    }
+  }
+  __syncthreads();
+  return qacc;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* __restrict__ lanes,
+                                                            DirectConst kc) {
+  __shared__ CSmem<CL> sm;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  double* w = reinterpret_cast<double*>(dyn_smem);
+  const unsigned q = CL > 1 ? cluster_rank() : 0u;
+  const DirectLane D = lanes[blockIdx.x / CL];
+  cluster_setup<CL>(sm);
+  Subst<CL> sub(D.LB, D.Binv, D.Cf, D.Db, w, sm, kc.n, kc.bw, (int)q);
+  const double part = cluster_integrate<CL>(kc, D, D.init_from_a0 ? D.a0 : nullptr, D.n_steps,
+                                            D.k0, q, sub, w, true);
+  const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
+  if (threadIdx.x == 0 && q == 0)
+    D.qoi_out[0] = kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s;
+  cluster_finish<CL>(sm, D);
+}
+
+// Parareal coarse sweep (Eq. 12), one cluster per sample; slice states
+// lane-major U/E/G[(sample*M + s) * n + i].
+template <int CL>
+__global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __restrict__ lanes,
+                                                        DirectConst kc, DirectChain ch) {
+  __shared__ CSmem<CL> sm;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  double* w = reinterpret_cast<double*>(dyn_smem);
+  const unsigned q = CL > 1 ? cluster_rank() : 0u;
+  const DirectLane D = lanes[blockIdx.x / CL];
+  const int n = kc.n;
+  const Own<CL> own{n, (int)q};
+  const int n_own = own.count();
+  const int sample = D.sample;
+  cluster_setup<CL>(sm);
+  Subst<CL> sub(D.LB, D.Binv, D.Cf, D.Db, w, sm, n, kc.bw, (int)q);
+  for (int s = ch.s_begin; s < ch.M - 1; ++s) {
+    const int64_t base = ((int64_t)sample * ch.M + s) * n;
+    cluster_integrate<CL>(kc, D, ch.U + base, ch.steps_per_slice,
+                          (int64_t)s * ch.steps_per_slice, q, sub, w, false);
+    double j2 = 0.0, u2 = 0.0;
+    for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
+      const int pi = own.row(idx);
+      if (pi >= n) continue;
+      const int i = __ldg(kc.perm + pi);
+      const double gn = D.a0[i];
+      const double un = ch.first_sweep ? gn : ch.E[base + i] + (gn - ch.G[base + i]);
+      const double du = un - ch.U[base + n + i];
+      j2 = fma(du, du, j2);
+      u2 = fma(un, un, u2);
+      ch.U[base + n + i] = un;
+      ch.G[base + i] = gn;
+    }
+    j2 = cluster_sum<CL>(cta_sum(j2, sm.red), sm, 0, q);
+    u2 = cluster_sum<CL>(cta_sum(u2, sm.red), sm, 1, q);   // also publishes U[s + 1]
+    if (threadIdx.x == 0 && q == 0) {
+      ch.jump2[(int64_t)sample * ch.M + s + 1] = j2;
+      ch.norm2[(int64_t)sample * ch.M + s + 1] = u2;
+    }
+    __syncthreads();
+  }
+  cluster_finish<CL>(sm, D);
+}
+
+// ---------------------------------------------------------------- block couplings
+// Per factor and block b: C_b = B_b L~_{b,b-1} stored [r][t], and
+// D_b^T = L~_{b+1,b} B_b stored [t][r] (zero where the neighbour block is absent).
+__global__ void __launch_bounds__(1024) k_block_couplings(const double* __restrict__ LBall,
+                                                        const double* __restrict__ Binv_all,
+                                                        int n, int bw, int64_t fstride, int nblk,
+                                                        double* __restrict__ Cf_all,
+                                                        double* __restrict__ Db_all) {
+  __shared__ double Bs[kB][kB + 1], O0[kB][kB + 1], O1[kB][kB + 1];
+  const int b = blockIdx.x, f = blockIdx.y;
+  const int r = threadIdx.y, c = threadIdx.x;
+  const double* LB = LBall + f * fstride;
+  const int64_t bo = ((int64_t)f * nblk + b) * kB * kB;
+  const int W = bw + 1;
+  Bs[r][c] = Binv_all[bo + r * kB + c];
+  // Off_blk[m][c] = L~(32 blk + m, 32 (blk - 1) + c)
+  auto off = [&](int blk, int m, int cc) -> double {
+    if (blk < 1 || blk >= nblk) return 0.0;
+    const int i = blk * kB + m, col = (blk - 1) * kB + cc;
+    if (i >= n || i - col > bw) return 0.0;
+    return LB[(int64_t)i * W + (col - i + bw)];
+  };
+  O0[r][c] = off(b, r, c);
+  O1[r][c] = off(b + 1, r, c);
+  __syncthreads();
+  double cf = 0.0, db = 0.0;
+#pragma unroll 8
+  for (int m = 0; m < kB; ++m) {
+    cf = fma(Bs[r][m], O0[m][c], cf);
+    db = fma(O1[r][m], Bs[m][c], db);
+  }
+  Cf_all[bo + r * kB + c] = cf;
+  Db_all[bo + r * kB + c] = db;
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <int CL>
+const void* propagate_fn() { return reinterpret_cast<const void*>(&k_cluster_propagate<CL>); }
+template <int CL>
+const void* chain_fn() { return reinterpret_cast<const void*>(&k_cluster_chain<CL>); }
+
+size_t cluster_smem(int n) { return (size_t)n * sizeof(double); }
+
+template <int CL>
+int set_attrs(size_t smem) {
+  MQS_CUDA_TRY(cudaFuncSetAttribute(propagate_fn<CL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  MQS_CUDA_TRY(cudaFuncSetAttribute(chain_fn<CL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  return MQS_OK;
+}
+
+template <int CL, class... Args>
+int launch_cl(const void* fn, int n_lanes, size_t smem, cudaStream_t st, Args... args) {
+  MQS_TRY(set_attrs<CL>(smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_lanes * CL));
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* argv[] = {(void*)&args...};
+  MQS_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, argv));
+  count_launch();
+  return MQS_OK;
+}
+
+template <int CL>
+int max_active_t(size_t smem) {
+  if (set_attrs<CL>(smem) != MQS_OK) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)CL);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, propagate_fn<CL>(), &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
+}
+
+}  // namespace
+
+int cluster_max_n() {
+  const size_t fixed = std::max(std::max(sizeof(CSmem<1>), sizeof(CSmem<2>)),
+                                std::max(sizeof(CSmem<4>), sizeof(CSmem<8>)));
+  return (int)((227 * 1024 - fixed - 1024) / sizeof(double));
+}
+
+int cluster_max_active(int CL, int n) {
+  static std::mutex mu;
+  static int cache[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
+  static int cache_n[4] = {-1, -1, -1, -1};
+  const int slot = CL == 1 ? 0 : CL == 2 ? 1 : CL == 4 ? 2 : CL == 8 ? 3 : -1;
+  if (slot < 0) return 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache_n[slot] == n && cache[slot][0] == dev) return cache[slot][1];
+  const size_t smem = cluster_smem(n);
+  int r = 0;
+  switch (CL) {
+    case 1: r = max_active_t<1>(smem); break;
+    case 2: r = max_active_t<2>(smem); break;
+    case 4: r = max_active_t<4>(smem); break;
+    case 8: r = max_active_t<8>(smem); break;
+  }
+  cache_n[slot] = n;
+  cache[slot][0] = dev;
+  cache[slot][1] = r;
+  return r;
+}
+
+int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
+                    double* Cf, double* Db, cudaStream_t st) {
+  const int nblk = (m.n_free + kB - 1) / kB;
+  const int64_t fstride = (int64_t)m.n_free * (m.bw + 1);
+  if (n_fac <= 0) return MQS_OK;
+  k_block_couplings<<<dim3((unsigned)nblk, (unsigned)n_fac), dim3(kB, kB), 0, st>>>(
+      LB, Binv, m.n_free, m.bw, fstride, nblk, Cf, Db);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return MQS_OK;
+}
+
+int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  const size_t smem = cluster_smem(kc.n);
+  switch (kc.cluster) {
+    case 1: return launch_cl<1>(propagate_fn<1>(), n_lanes, smem, st, d_lanes, kc);
+    case 2: return launch_cl<2>(propagate_fn<2>(), n_lanes, smem, st, d_lanes, kc);
+    case 4: return launch_cl<4>(propagate_fn<4>(), n_lanes, smem, st, d_lanes, kc);
+    case 8: return launch_cl<8>(propagate_fn<8>(), n_lanes, smem, st, d_lanes, kc);
+  }
+  set_error("unsupported cluster size %d", kc.cluster);
+  return MQS_EINVAL;
+}
+
+int launch_cluster_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                         const DirectChain& ch, cudaStream_t st) {
+  if (n_lanes <= 0) return MQS_OK;
+  const size_t smem = cluster_smem(kc.n);
+  switch (kc.cluster) {
+    case 1: return launch_cl<1>(chain_fn<1>(), n_lanes, smem, st, d_lanes, kc, ch);
+    case 2: return launch_cl<2>(chain_fn<2>(), n_lanes, smem, st, d_lanes, kc, ch);
+    case 4: return launch_cl<4>(chain_fn<4>(), n_lanes, smem, st, d_lanes, kc, ch);
+    case 8: return launch_cl<8>(chain_fn<8>(), n_lanes, smem, st, d_lanes, kc, ch);
+  }
+  set_error("unsupported cluster size %d", kc.cluster);
+  return MQS_EINVAL;
+}
+
+}  // namespace mqs

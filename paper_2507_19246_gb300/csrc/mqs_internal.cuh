@@ -158,6 +158,8 @@ struct DirectLane {
   const double* LB;        // this lane's band Cholesky factor [n][bw+1]
   const double* invd;      // its reciprocal diagonal [n]
   const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
+  const double* Cf;        // block couplings B_b L~_{b,b-1} [n/32][32][32] (cluster kernels)
+  const double* Db;        // block couplings L~_{b+1,b} B_b [n/32][32][32] (cluster kernels)
   const float* LBf;        // FP32 factor, reciprocal diagonal and block inverses (mixed)
   const float* invdf;
   const float* Binvf;
@@ -177,6 +179,7 @@ struct DirectConst {
   const int32_t* rowptr;
   const int32_t* colidx;
   const int32_t* iperm;    // original -> band ordering
+  const int32_t* perm;     // band ordering -> original
   const double* M;         // [nnz][vs] sample values
   const double* K;
   int64_t vs;
@@ -187,7 +190,7 @@ struct DirectConst {
   int32_t mixed;           // 1: FP32 factor with FP64 refinement sweeps
   double tol2;             // mixed: stop when ||b - A x||^2 <= tol2 ||b||^2
   int32_t max_sweeps;      // mixed: refinement sweep limit per step
-  int32_t pad2_;
+  int32_t cluster;         // 0: one-CTA kernels of mqs_direct.cu; 1, 2, 4, 8: CTAs per lane
 };
 
 struct DirectChain {
@@ -205,6 +208,16 @@ int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
 int direct_smem_max_n(int mixed);
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st);
+
+// mqs_cluster.cu: FP64 stepping with the block solve spread over warps and a
+// lane split over a cluster of `cluster` CTAs (work vector in shared memory)
+int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
+                    double* Cf, double* Db, cudaStream_t st);
+int cluster_max_n();
+int cluster_max_active(int CL, int n);
+int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
+int launch_cluster_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
+                         const DirectChain& ch, cudaStream_t st);
 
 // launchers (mqs_team.cu)
 int launch_propagate(const TileDesc* d_tiles, int n_tiles, int L, int C, int precision,

@@ -21,7 +21,7 @@ from . import build as _build
 MQS_OK, MQS_EINVAL, MQS_ENOMEM, MQS_ECUDA, MQS_ENOTCONV = 0, -1, -2, -3, -4
 MQS_FP64, MQS_MIXED = 0, 1
 MQS_QOI_ENERGY, MQS_QOI_JOULE = 0, 1
-MQS_ST_NOTCONV, MQS_ST_NONFINITE, MQS_ST_NOTSPD = 1, 2, 4
+MQS_ST_NOTCONV, MQS_ST_NONFINITE, MQS_ST_NOTSPD, MQS_ST_TIMEOUT = 1, 2, 4, 8
 MQS_SOLVER_PCG, MQS_SOLVER_BANDED = 0, 1
 
 _lib = None

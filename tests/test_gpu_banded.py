@@ -185,3 +185,97 @@ def test_banded_mixed_parareal(ctx, mqs):
     q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
     assert abs(K - ref["iters"]) <= 1
     assert abs(q[0, 0] - q_ref) <= 1e-6 * abs(q_ref)
+
+
+# ---------------------------------------------------------------- cluster-split stepping
+# MQS_DIRECT_CLUSTER = 0 selects the one-CTA kernels; 1, 2, 4, 8 the stepping
+# kernels whose block substitution is spread over warps and over a cluster of
+# that many CTAs per lane.
+CLUSTERS = ["0", "1", "2", "4", "8"]
+
+
+@pytest.mark.parametrize("cluster", CLUSTERS)
+def test_cluster_split_level_pair(ctx, mqs, monkeypatch, cluster):
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", cluster)
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(5, 2, seed=11)
+    dt1, dt0 = configs.level_dt(2), configs.level_dt(1)
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, configs.PERIOD / 4, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 2, dt1, dt_prev=dt0)
+    q, st = ctx.read_qoi(b)
+    a, ac = ctx.read_state(b, 0), ctx.read_state(b, 1)
+    assert not st.any()
+    for s in range(p.shape[0]):
+        qf, af, _ = stepper.solve_sample(mesh, p[s], dt1, 64, stepper.QOI_JOULE)
+        qc, acc, _ = stepper.solve_sample(mesh, p[s], dt0, 32, stepper.QOI_JOULE)
+        assert abs(q[s, 0] - qf) <= TOL * abs(qf) and abs(q[s, 1] - qc) <= TOL * abs(qc), s
+        assert _rel(a[s], af) <= TOL and _rel(ac[s], acc) <= TOL, s
+
+
+@pytest.mark.parametrize("cluster", CLUSTERS)
+def test_cluster_split_energy_ragged_small(ctx, mqs, monkeypatch, cluster):
+    """n = 49 free unknowns: two 32-row blocks, the second ragged; energy QoI."""
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", cluster)
+    mesh = meshes.unit_square(8)
+    p = params.square_samples(3)
+    dt = configs.PERIOD / 40
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 13 * dt, 50.0, mqs.MQS_QOI_ENERGY)
+    ctx.propagate(b, 0, dt)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    for s in range(3):
+        qo, ao, _ = stepper.solve_sample(mesh, p[s], dt, 13, stepper.QOI_ENERGY)
+        assert abs(q[s, 0] - qo) <= TOL * abs(qo) and _rel(a[s], ao) <= TOL, s
+
+
+@pytest.mark.parametrize("cluster", CLUSTERS)
+def test_cluster_split_parareal(ctx, mqs, monkeypatch, cluster):
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", cluster)
+    mesh = meshes.annulus("5k")
+    p = params.annulus_nominal(1)
+    n_steps, M, cf, tol = 128, 8, 4, 1e-8
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+    K = ctx.propagate(b, 0, dt, n_slices=M, coarse_factor=cf, max_par_iters=M, par_tol=tol)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    d = fem.Discretisation(mesh, p[0])
+    ref = parareal.parareal_sample(d, dt, n_steps, M, cf, tol, stepper.QOI_JOULE)
+    q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
+    assert K == ref["iters"]
+    assert abs(q[0, 0] - q_ref) <= TOL * abs(q_ref)
+    assert _rel(a[0], ref["a_end"]) <= TOL
+
+
+@pytest.mark.parametrize("cluster", ["2", "8"])
+def test_cluster_split_lane_is_independent_of_batch(ctx, mqs, monkeypatch, cluster):
+    """With the cluster size fixed, a sample's result does not depend on the
+    other lanes of its launch: bitwise equal alone and inside a batch."""
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", cluster)
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(6, 1, seed=5)
+    mid = ctx.upload_mesh(mesh)
+    out = []
+    for pp in (p, p[4:5]):
+        b = ctx.set_samples(mid, pp)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, configs.PERIOD / 8, 50.0, mqs.MQS_QOI_JOULE)
+        ctx.propagate(b, 1, configs.level_dt(1))
+        out.append((ctx.read_qoi(b)[0], ctx.read_state(b, 0)))
+    assert out[0][0][4, 0] == out[1][0][0, 0]
+    assert np.array_equal(out[0][1][4], out[1][1][0])
