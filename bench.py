@@ -356,15 +356,20 @@ def run_ours(args, wl, rank, world, dist):
     else:
         bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
         achieved = hbm_gbs
+    # DRAM traffic per launch from a recorded ncu capture of the same kernel
+    # source (keyed by workload, precision, solver and kernel; null once the
+    # source file of that kernel has changed since the capture)
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     try:
         import hashlib
-        tr = json.load(open(traffic_path)).get(f"{wl['name']}:{args.precision}:{dominant}")
-        src = os.path.join(ROOT, "paper_2507_19246_gb300", "csrc", "mqs_team.cu")
-        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if tr and tr.get("mqs_team_sha256_16") == cur:
-            traffic = tr["bytes_per_launch"]
+        key = f"{wl['name']}:{args.precision}:{args.solver}:{dominant}"
+        tr = json.load(open(traffic_path)).get(key)
+        if tr:
+            src = os.path.join(ROOT, "paper_2507_19246_gb300", "csrc", tr["source_file"])
+            cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            if tr.get("source_sha256_16") == cur:
+                traffic = tr["bytes_per_launch"]
     except Exception:
         traffic = None
     # CPU baseline: the oracle's serial fine propagator on a bounded sample

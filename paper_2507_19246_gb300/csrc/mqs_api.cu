@@ -43,7 +43,7 @@ struct FactorSet {
   double dt = 0.0;
   bool have64 = false, have32 = false, have_cpl = false;
   DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
-  DevBuf Cf, Db;                // [samples][n/32][32][32] block couplings (cluster kernels)
+  DevBuf C1, C2, D1, D2;        // [samples][n/32][32][32] block couplings (cluster kernels)
   DevBuf LBf, invdf, Binvf;     // FP32 factor (mixed precision)
 };
 
@@ -596,10 +596,10 @@ FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool 
 int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
   if (f.have_cpl) return MQS_OK;
   const size_t bstride = (size_t)block_count(m.n_free) * 32 * 32;
-  MQS_TRY(f.Cf.ensure(bstride * b.n * sizeof(double)));
-  MQS_TRY(f.Db.ensure(bstride * b.n * sizeof(double)));
-  MQS_TRY(block_couplings(m, b.n, f.LB.as<double>(), f.Binv.as<double>(), f.Cf.as<double>(),
-                          f.Db.as<double>(), ctx->c.stream));
+  for (DevBuf* x : {&f.C1, &f.C2, &f.D1, &f.D2})
+    MQS_TRY(x->ensure(bstride * b.n * sizeof(double)));
+  MQS_TRY(block_couplings(m, b.n, f.LB.as<double>(), f.Binv.as<double>(), f.C1.as<double>(),
+                          f.C2.as<double>(), f.D1.as<double>(), f.D2.as<double>(), ctx->c.stream));
   f.have_cpl = true;
   return MQS_OK;
 }
@@ -656,8 +656,11 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   d.LB = f.LB.as<double>() + fstride * sample;
   d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
   d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
-  d.Cf = f.Cf.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
-  d.Db = f.Db.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  const size_t bo = (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  d.C1 = f.C1.as<double>() + bo;
+  d.C2 = f.C2.as<double>() + bo;
+  d.D1 = f.D1.as<double>() + bo;
+  d.D2 = f.D2.as<double>() + bo;
   d.LBf = f.LBf.as<float>() + fstride * sample;
   d.invdf = f.invdf.as<float>() + (size_t)m.n_free * sample;
   d.Binvf = f.Binvf.as<float>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;

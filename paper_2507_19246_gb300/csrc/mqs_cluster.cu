@@ -12,22 +12,28 @@
 // lane may be split over a cluster of CL CTAs on CL SMs.
 //
 // Algebra (unit lower factor L~ = D^-1 L, 32-row blocks, B_b = L~_bb^-1):
-//   forward  L~ y = w:    y_b = B_b (w_b - P_b) - C_b y_{b-1},
-//                         C_b = B_b L~_{b,b-1},   P_b = sum_{k <= b-2} L~_bk y_k
-//   backward L~^T u = y:  u_b = B_b^T (y_b - Q_b) - D_b u_{b+1},
-//                         D_b = B_b^T L~_{b+1,b}^T, Q_b = sum_{k >= b+2} L~_kb^T u_k
-// C_b and D_b^T = L~_{b+1,b} B_b are precomputed with the factor.  P and Q
-// of block b are computed while block b-1 (b+1) is being solved.
+//   forward  L~ y = w:    y_b = B_b (w_b - P_b) - C1_b y_{b-1} - C2_b y_{b-2},
+//                         C1_b = B_b L~_{b,b-1}, C2_b = B_b L~_{b,b-2},
+//                         P_b = sum_{k <= b-3} L~_bk y_k
+//   backward L~^T u = y:  u_b = B_b^T (y_b - Q_b) - D1_b u_{b+1} - D2_b u_{b+2},
+//                         D1_b = B_b^T L~_{b+1,b}^T, D2_b = B_b^T L~_{b+2,b}^T,
+//                         Q_b = sum_{k >= b+3} L~_kb^T u_k
+// The couplings are precomputed with the factor.  Warp roles: GEMV warps form
+// s_b = w_b - P_b (or y_b - Q_b) for the block solved two rounds later; the
+// solve warps form pre_b = B_b s_b - C2_b y_{b-2} one round ahead, so that the
+// critical path of a round is only v_b = pre_b - C1_b y_{b-1} and its
+// exchange.  The two warp groups hand data over through release/acquire
+// progress counters in shared memory, never through a CTA-wide barrier.
 //
 // Cluster split: every CTA keeps a full copy of the permuted work vector in
 // shared memory and owns rows q*R .. q*R+R-1 (R = 32/CL) of every block, in
-// the band ordering.  Per block it computes P (Q) for its own rows and its
-// share of the block solve, v_q = B_b[:, own] s_b[own] - C_b[:, own] y_{b-1}[own],
-// which it sends to every CTA of the cluster with asynchronous DSMEM stores
-// that complete on the receiver's mbarrier (no fence on the sending side, no
-// cluster barrier per block); each CTA adds the CL shares in rank order, so
-// all copies hold identical values.  Waits are bounded: a wait that runs out
-// sets MQS_ST_TIMEOUT on the lane and the kernel skips every later wait.
+// the band ordering.  Per block it computes s for its own rows and its share
+// of the block solve, v_q = pre_q - C1_b[:, own] y_{b-1}[own], which it sends
+// to every CTA of the cluster with asynchronous DSMEM stores that complete on
+// the receiver's mbarrier (no fence on the sending side, no cluster barrier
+// per block); each CTA adds the CL shares in rank order, so all copies hold
+// identical values.  Waits are bounded: a wait that runs out sets
+// MQS_ST_TIMEOUT on the lane and the kernel skips every later wait.
 // Node-wise work (right-hand side, y = M a, QoI) is split by the same row
 // ownership, so a step exchanges no data through global memory except the new
 // state a1, which is published by a cluster barrier before y = M a1.
@@ -63,17 +69,20 @@ struct Split {
   static constexpr int TB = R / GW;              // backward: own columns per GEMV warp
   static constexpr int KG = 32 / TB;             // backward: row groups per own column
   static constexpr int TPL = (R + 3) / 4;        // own rows per solve lane
+  static constexpr int LV = R >= 4 ? 2 : (R == 2 ? 1 : 0);   // solve reduction levels
   static_assert(R * H == 4 * GW && H <= 4, "forward items fill the GEMV warps, rows stay in a warp");
   static_assert(TB >= 1 && TB * GW == R, "backward columns fill the GEMV warps");
   static_assert(kSW + GW <= kNW, "warp roles");
-  static_assert(2 * TPL <= kPF, "solve prefetch fits the register array");
+  static_assert(3 * TPL <= kPF, "solve prefetch fits the register array");
 };
 
 template <int CL>
 struct CSmem {
   double V[2][CL][kB];                       // block-solve shares [round parity][rank][row]
-  double s[2][Split<CL>::R];                 // own rows' right-hand side of the block solve
+  double s[4][Split<CL>::R];                 // own rows' s of the block solves, ring by round
   unsigned long long mbar[2];                // share arrivals of V[0], V[1]
+  int ydone;                                 // rounds whose solved block is in the copy
+  int sdone;                                 // rounds whose s is in the ring
   int err;                                   // a wait ran out
   double red[kNW];
   double cred[CL][2];                        // per-rank partial sums for cluster reductions
@@ -128,6 +137,31 @@ __device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t parity, int* e
   for (int it = 0; it < kWaitLimit; ++it)
     if (mbar_try_wait(mbar, parity)) return;
   *reinterpret_cast<volatile int*>(err) = 1;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.cta.shared.s32 [%0], %1;" :: "r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+
+// Wait until a progress counter reaches target, at most kWaitLimit polls.
+__device__ __forceinline__ void wait_count(const int* p, int target, int* err) {
+  if (*reinterpret_cast<volatile int*>(err)) return;
+  for (int it = 0; it < kWaitLimit; ++it) {
+    if (ld_acquire(p) >= target) return;
+    __nanosleep(32);
+  }
+  *reinterpret_cast<volatile int*>(err) = 1;
+}
+
+// Barrier of one warp group (ids 1, 2; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(threads) : "memory");
 }
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -189,8 +223,10 @@ struct Subst {
   using S = Split<CL>;
   const double* __restrict__ LB;
   const double* __restrict__ Binv;
-  const double* __restrict__ Cf;
-  const double* __restrict__ Db;
+  const double* __restrict__ C1;   // [b][r][t]
+  const double* __restrict__ C2;   // [b][r][t]
+  const double* __restrict__ D1;   // D1_b^T: [b][t][r]
+  const double* __restrict__ D2;   // D2_b^T: [b][t][r]
   double* w;
   CSmem<CL>& sm;
   int n, bw, W, nblk, q;
@@ -201,10 +237,9 @@ struct Subst {
   int s_r, s_g;          // solve lane: block row, term group
   int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
 
-  __device__ Subst(const double* LB_, const double* Binv_, const double* Cf_, const double* Db_,
-                   double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
-      : LB(LB_), Binv(Binv_), Cf(Cf_), Db(Db_), w(w_), sm(sm_), n(n_), bw(bw_), W(bw_ + 1),
-        nblk((n_ + kB - 1) / kB), q(q_) {
+  __device__ Subst(const DirectLane& D, double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
+      : LB(D.LB), Binv(D.Binv), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), w(w_), sm(sm_), n(n_),
+        bw(bw_), W(bw_ + 1), nblk((n_ + kB - 1) / kB), q(q_) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     gw = warp - kSW;
@@ -221,17 +256,22 @@ struct Subst {
   __device__ bool is_solve() const { return warp < kSW; }
   __device__ bool is_gemv() const { return warp >= kSW && warp < kSW + S::GW; }
   __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
+  // own row t of block blk from the copy (0 past n)
+  __device__ double own_val(int blk, int t) const {
+    const int row = blk * kB + q * S::R + t;
+    return row < n ? w[row] : 0.0;
+  }
 
-  // GEMV of round g: the partial sums of the block solved in round g + 1,
-  // over the part of the band already known when round g starts.
-  __device__ GemvDesc gemv_desc(int g) const {
+  // GEMV items of round j's s: forward, row i of block j over the columns of
+  // blocks <= j - 3; backward, column c of block bt over the rows of blocks
+  // >= bt + 3 (both known once round j - 2 has gathered its block).
+  __device__ GemvDesc gemv_desc(int j) const {
     GemvDesc d{0, 0, 0, 0, 0};
-    const int g1 = g + 1;
-    if (g1 >= 2 * nblk) return d;
-    if (g1 < nblk) {   // forward: row i of block g1, columns of blocks <= g1 - 2
-      const int i = g1 * kB + q * S::R + f_t;
+    if (j < 2 || j >= 2 * nblk || j == nblk) return d;
+    if (j < nblk) {
+      const int i = j * kB + q * S::R + f_t;
       if (i >= n) return d;
-      const int lo = max(0, i - bw), hi = g * kB;
+      const int lo = max(0, i - bw), hi = (j - 2) * kB;
       const int c0 = lo + 8 * f_h + f_g, st = 8 * S::H;
       if (c0 >= hi) return d;
       d.cnt = (hi - c0 + st - 1) / st;
@@ -239,13 +279,13 @@ struct Subst {
       d.step = st;
       d.w0 = c0;
       d.wstep = st;
-    } else {           // backward: column c of block bt, rows of blocks >= bt + 2
-      const int bt = 2 * nblk - 1 - g1;
+    } else {
+      const int bt = 2 * nblk - 1 - j;
       const int c = bt * kB + q * S::R + b_t;
       if (c >= n) return d;
       const int kend = min(n - 1, c + bw);
       const int st = S::KG;
-      const int k0 = (bt + 2) * kB + b_kg;
+      const int k0 = (bt + 3) * kB + b_kg;
       if (k0 > kend) return d;
       d.cnt = (kend - k0) / st + 1;
       d.off = (int64_t)k0 * W + (c - k0 + bw);
@@ -267,144 +307,180 @@ struct Subst {
     }
   }
 
-  // Block-solve operands of round g for this solve lane: pf[2j] = B entry,
-  // pf[2j+1] = coupling entry, own row t = s_g + 4j.
-  __device__ void solve_load(int g, double (&pf)[kPF]) const {
-    if (g >= 2 * nblk) return;
-    const bool fwd = g < nblk;
-    const int b = block_of(g);
-    const double* Bb = Binv + (int64_t)b * kB * kB;
-#pragma unroll
-    for (int j = 0; j < S::TPL; ++j) {
-      const int t = s_g + 4 * j;
-      double bv = 0.0, cv = 0.0;
-      if (t < S::R) {
-        const int tc = q * S::R + t;
-        if (fwd) {
-          bv = __ldg(Bb + s_r * kB + tc);
-          if (b >= 1) cv = __ldg(Cf + (int64_t)b * kB * kB + s_r * kB + tc);
-        } else {
-          bv = __ldg(Bb + tc * kB + s_r);
-          if (b + 1 < nblk) cv = __ldg(Db + (int64_t)b * kB * kB + tc * kB + s_r);
-        }
-      }
-      pf[2 * j] = bv;
-      pf[2 * j + 1] = cv;
-    }
-  }
-
-  // GEMV of round g (see gemv_desc): completes the own rows' sums inside the
-  // warp and stores the right-hand side s of the block solved in round g + 1.
-  // The block after the last forward one takes its s in that round (phase A).
-  // Once the products are formed, the loads of round g + 1 are issued (into
-  // pf, cur) so that they overlap the reduction.
-  __device__ void gemv_round(int g, GemvDesc& cur, double (&pf)[kPF]) {
-    // every FP64 warp instruction costs the same however many lanes are
-    // active, so the loop stops at the longest item of the warp; two
-    // accumulators halve the dependent chain
+  // Band products of round j's item (values in pf), then the loads of round
+  // j + 1 (into pf, cur) so that they overlap the reduction; stores s of the
+  // own rows into the ring.  Every FP64 warp instruction costs the same
+  // however many lanes are active, so the loop stops at the longest item of
+  // the warp; two accumulators halve the dependent chain.
+  __device__ void gemv_round(int j, GemvDesc& cur, double (&pf)[kPF]) {
     const int cmax = __reduce_max_sync(kFull, cur.cnt);
     double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-    for (int j = 0; j < kPF; j += 2) {
-      if (j >= cmax) break;
-      const double x0 = j < cur.cnt ? w[cur.w0 + j * cur.wstep] : 0.0;
-      acc0 = fma(pf[j], x0, acc0);
-      if (j + 1 >= cmax) break;
-      const double x1 = j + 1 < cur.cnt ? w[cur.w0 + (j + 1) * cur.wstep] : 0.0;
-      acc1 = fma(pf[j + 1], x1, acc1);
+    for (int k = 0; k < kPF; k += 2) {
+      if (k >= cmax) break;
+      const double x0 = k < cur.cnt ? w[cur.w0 + k * cur.wstep] : 0.0;
+      acc0 = fma(pf[k], x0, acc0);
+      if (k + 1 >= cmax) break;
+      const double x1 = k + 1 < cur.cnt ? w[cur.w0 + (k + 1) * cur.wstep] : 0.0;
+      acc1 = fma(pf[k + 1], x1, acc1);
     }
-    for (int j = kPF; j < cmax; ++j)
-      if (j < cur.cnt) acc0 = fma(__ldg(LB + cur.off + j * cur.step), w[cur.w0 + j * cur.wstep], acc0);
-    cur = gemv_desc(g + 1);
+    for (int k = kPF; k < cmax; ++k)
+      if (k < cur.cnt) acc0 = fma(__ldg(LB + cur.off + k * cur.step), w[cur.w0 + k * cur.wstep], acc0);
+    cur = gemv_desc(j + 1);
     gemv_load(cur, pf);
     double acc = acc0 + acc1;
-    const int g1 = g + 1;
-    if (g1 >= 2 * nblk || g1 == nblk) return;
-    double* s_next = sm.s[g1 & 1];
-    if (g1 < nblk) {
+    double* sj = sm.s[j & 3];
+    if (j < nblk) {
       acc += __shfl_xor_sync(kFull, acc, 1);
       acc += __shfl_xor_sync(kFull, acc, 2);
       acc += __shfl_xor_sync(kFull, acc, 4);
       if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 8);
       if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 16);
       if (f_g == 0 && f_h == 0) {
-        const int row = g1 * kB + q * S::R + f_t;
-        s_next[f_t] = row < n ? w[row] - acc : 0.0;
+        const int row = j * kB + q * S::R + f_t;
+        sj[f_t] = row < n ? w[row] - acc : 0.0;
       }
     } else {
 #pragma unroll
       for (int o = S::TB; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
       if (b_kg == 0) {
-        const int row = (2 * nblk - 1 - g1) * kB + q * S::R + b_t;
-        s_next[b_t] = row < n ? w[row] - acc : 0.0;
+        const int row = (2 * nblk - 1 - j) * kB + q * S::R + b_t;
+        sj[b_t] = row < n ? w[row] - acc : 0.0;
       }
     }
+  }
+
+  // Solve-lane operands: pf[3k] coupling to the last block (round g),
+  // pf[3k+1] B entry and pf[3k+2] coupling two blocks back (round g + 1),
+  // own row t = s_g + 4k.
+  __device__ void solve_load(int g, double (&pf)[kPF]) const {
+    const int G = 2 * nblk;
+#pragma unroll
+    for (int k = 0; k < S::TPL; ++k) {
+      const int t = s_g + 4 * k;
+      double c1 = 0.0, bv = 0.0, c2 = 0.0;
+      if (t < S::R) {
+        const int tc = q * S::R + t;
+        if (g < G) {
+          const int b = block_of(g);
+          const int64_t o = (int64_t)b * kB * kB;
+          if (g < nblk) {
+            if (b >= 1) c1 = __ldg(C1 + o + s_r * kB + tc);
+          } else if (g >= nblk + 1) {
+            c1 = __ldg(D1 + o + tc * kB + s_r);
+          }
+        }
+        const int g1 = g + 1;
+        if (g1 < G && g1 != nblk) {
+          const int b1 = block_of(g1);
+          const int64_t o = (int64_t)b1 * kB * kB;
+          if (g1 < nblk) {
+            bv = __ldg(Binv + o + s_r * kB + tc);
+            if (b1 >= 2) c2 = __ldg(C2 + o + s_r * kB + tc);
+          } else {
+            bv = __ldg(Binv + o + tc * kB + s_r);
+            if (b1 + 2 < nblk) c2 = __ldg(D2 + o + tc * kB + s_r);
+          }
+        }
+      }
+      pf[3 * k] = c1;
+      pf[3 * k + 1] = bv;
+      pf[3 * k + 2] = c2;
+    }
+  }
+
+  __device__ double reduce_terms(double v) const {
+    if (S::LV >= 1) v += __shfl_xor_sync(kFull, v, 8);
+    if (S::LV >= 2) v += __shfl_xor_sync(kFull, v, 16);
+    return v;
   }
 
   // Forward then backward substitution; on return w holds u (all rows).
   __device__ void run(double (&pf)[kPF]) {
     const int G = 2 * nblk;
-    GemvDesc cur{0, 0, 0, 0, 0};
-    if (is_gemv()) {
-      gemv_round(-1, cur, pf);   // block 0: s = own right-hand sides; loads of round 0
-    } else if (is_solve()) {
-      solve_load(0, pf);
+    if (threadIdx.x == 0) {
+      sm.ydone = -1;
+      sm.sdone = -1;
     }
     __syncthreads();
-    const int rl = s_r - q * S::R;                  // own-row index of a solve lane
-    const bool own = is_solve() && rl >= 0 && rl < S::R;
-    for (int g = 0; g <= G; ++g) {
-      const bool fwd = g < nblk;
-      const int b = block_of(g);
-      // ---------------- phase A: gather the last block's shares into the copy
-      if ((CL > 1 && g >= 1) || g == nblk) {
-        if (is_solve()) {
-          double yv = 0.0;
-          if (CL > 1 && g >= 1) {
-            const int bp = block_of(g - 1);
-            const int64_t r = rounds + g - 1;   // round whose shares arrive
-            const uint32_t mb = smem_addr(&sm.mbar[r & 1]);
-            mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
-            if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
-            const double* Vb = &sm.V[(g - 1) & 1][0][0];
-            double acc = s_g < CL ? Vb[s_g * kB + s_r] : 0.0;
-            for (int p = s_g + 4; p < CL; p += 4) acc += Vb[p * kB + s_r];
-            if (CL > 1) acc += __shfl_xor_sync(kFull, acc, 8);
-            if (CL > 2) acc += __shfl_xor_sync(kFull, acc, 16);
-            yv = acc;
-            const int row = bp * kB + s_r;
-            if (s_g == 0 && row < n) w[row] = yv;
-          }
-          if (g == nblk && own && s_g == 0) {   // first backward block: s = y (Q = 0)
-            const int row = (nblk - 1) * kB + s_r;
-            sm.s[g & 1][rl] = row < n ? (CL > 1 ? yv : w[row]) : 0.0;
-          }
+    if (is_gemv()) {
+      // s of rounds 0 and 1: own right-hand sides (no band part yet)
+      const int gt = threadIdx.x - kSW * 32;
+      for (int j = 0; j < 2; ++j)
+        if (j < G && j != nblk && gt < S::R) {
+          const int row = j * kB + q * S::R + gt;
+          sm.s[j & 3][gt] = row < n ? w[row] : 0.0;
         }
-        __syncthreads();
+      GemvDesc cur = gemv_desc(2);
+      gemv_load(cur, pf);
+      group_sync(2, S::GW * 32);
+      if (gt == 0) st_release(&sm.sdone, 1);
+      for (int g = 0; g + 2 < G; ++g) {
+        const int j = g + 2;
+        wait_count(&sm.ydone, g, &sm.err);
+        if (j != nblk) {
+          gemv_round(j, cur, pf);
+        } else {
+          cur = gemv_desc(j + 1);
+          gemv_load(cur, pf);
+        }
+        group_sync(2, S::GW * 32);
+        if (gt == 0) st_release(&sm.sdone, j);
       }
-      if (g == G) break;
-      // ---------------- phase B: block solve share, GEMV one block ahead
-      if (is_solve()) {
-        const double* sb = sm.s[g & 1];
-        double v0 = 0.0, v1 = 0.0;
+    } else if (is_solve()) {
+      // pre of round 0: B_0 s_0
+      wait_count(&sm.sdone, 0, &sm.err);
+      double pre = 0.0;
 #pragma unroll
-        for (int j = 0; j < S::TPL; ++j) {
-          const int t = s_g + 4 * j;
-          if (t < S::R) {
-            double yo = 0.0;
-            if (fwd) {
-              if (b >= 1) yo = w[(b - 1) * kB + q * S::R + t];
-            } else {
-              const int row = (b + 1) * kB + q * S::R + t;
-              if (b + 1 < nblk && row < n) yo = w[row];
-            }
-            v0 = fma(pf[2 * j], sb[t], v0);
-            v1 = fma(-pf[2 * j + 1], yo, v1);
+      for (int k = 0; k < S::TPL; ++k) {
+        const int t = s_g + 4 * k;
+        if (t < S::R) pre = fma(__ldg(Binv + s_r * kB + q * S::R + t), sm.s[0][t], pre);
+      }
+      solve_load(0, pf);
+      for (int g = 0; g <= G; ++g) {
+        // [A] the shares of round g - 1 into the copy
+        if (CL > 1 && g >= 1) {
+          const int bp = block_of(g - 1);
+          const int64_t r = rounds + g - 1;
+          const uint32_t mb = smem_addr(&sm.mbar[r & 1]);
+          mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
+          if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
+          const double* Vb = &sm.V[(g - 1) & 1][0][0];
+          double acc = s_g < CL ? Vb[s_g * kB + s_r] : 0.0;
+          for (int p = s_g + 4; p < CL; p += 4) acc += Vb[p * kB + s_r];
+          if (CL > 1) acc += __shfl_xor_sync(kFull, acc, 8);
+          if (CL > 2) acc += __shfl_xor_sync(kFull, acc, 16);
+          const int row = bp * kB + s_r;
+          if (s_g == 0 && row < n) w[row] = acc;
+        }
+        if (g == G) break;
+        group_sync(1, kSW * 32);
+        if (threadIdx.x == 0) st_release(&sm.ydone, g);
+        const bool fwd = g < nblk;
+        const int b = block_of(g);
+        // [B] first backward block: pre = B_b^T y_b (no band part, no couplings)
+        if (g == nblk) {
+          pre = 0.0;
+#pragma unroll
+          for (int k = 0; k < S::TPL; ++k) {
+            const int t = s_g + 4 * k;
+            if (t < S::R)
+              pre = fma(__ldg(Binv + (int64_t)b * kB * kB + (q * S::R + t) * kB + s_r),
+                        own_val(b, t), pre);
           }
         }
-        double v = v0 + v1;
-        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 8);
-        if (S::R > 2) v += __shfl_xor_sync(kFull, v, 16);
+        // [C] v = pre - C1 y_{b-1} (forward) or pre - D1 u_{b+1} (backward)
+        const bool c1 = fwd ? b >= 1 : g >= nblk + 1;
+        const int bp = block_of(g - 1);
+        double y1[S::TPL];
+        double v0 = pre, v1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < S::TPL; ++k) {
+          const int t = s_g + 4 * k;
+          y1[k] = (c1 && t < S::R) ? own_val(bp, t) : 0.0;
+          if (t < S::R) v1 = fma(-pf[3 * k], y1[k], v1);
+        }
+        const double v = reduce_terms(v0 + v1);
         if constexpr (CL == 1) {
           const int row = b * kB + s_r;
           if (s_g == 0 && row < n) w[row] = v;
@@ -413,17 +489,31 @@ struct Subst {
           const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
           for (int p = s_g; p < CL; p += 4) {
             if (p == q)
-              sm.V[g & 1][q][s_r] = v;   // own share: ordered by the CTA barrier below
+              sm.V[g & 1][q][s_r] = v;   // own share: ordered by the group barrier of the next round
             else
               st_async(map_rank(la, p), v, map_rank(lm, p));
           }
         }
+        // [D] pre of round g + 1: B s - C2 y_{b'-2} (forward) or B^T s - D2 u_{b'+2}
+        const int g1 = g + 1;
+        if (g1 < G && g1 != nblk) {
+          wait_count(&sm.sdone, g1, &sm.err);
+          const double* s1 = sm.s[g1 & 3];
+          double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+          for (int k = 0; k < S::TPL; ++k) {
+            const int t = s_g + 4 * k;
+            if (t < S::R) {
+              p0 = fma(pf[3 * k + 1], s1[t], p0);
+              p1 = fma(-pf[3 * k + 2], y1[k], p1);   // two blocks back = this round's last block
+            }
+          }
+          pre = p0 + p1;
+        }
         solve_load(g + 1, pf);
-      } else if (is_gemv()) {
-        gemv_round(g, cur, pf);
       }
-      __syncthreads();
     }
+    __syncthreads();
     rounds += G;
   }
 };
@@ -570,7 +660,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
   const unsigned q = CL > 1 ? cluster_rank() : 0u;
   const DirectLane D = lanes[blockIdx.x / CL];
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D.LB, D.Binv, D.Cf, D.Db, w, sm, kc.n, kc.bw, (int)q);
+  Subst<CL> sub(D, w, sm, kc.n, kc.bw, (int)q);
   const double part = cluster_integrate<CL>(kc, D, D.init_from_a0 ? D.a0 : nullptr, D.n_steps,
                                             D.k0, q, sub, w, true);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
@@ -594,7 +684,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   const int n_own = own.count();
   const int sample = D.sample;
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D.LB, D.Binv, D.Cf, D.Db, w, sm, n, kc.bw, (int)q);
+  Subst<CL> sub(D, w, sm, n, kc.bw, (int)q);
   for (int s = ch.s_begin; s < ch.M - 1; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
     cluster_integrate<CL>(kc, D, ch.U + base, ch.steps_per_slice,
@@ -624,38 +714,48 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
 }
 
 // ---------------------------------------------------------------- block couplings
-// Per factor and block b: C_b = B_b L~_{b,b-1} stored [r][t], and
-// D_b^T = L~_{b+1,b} B_b stored [t][r] (zero where the neighbour block is absent).
+// Per factor and block b: C1_b = B_b L~_{b,b-1}, C2_b = B_b L~_{b,b-2} stored
+// [r][t]; D1_b^T = L~_{b+1,b} B_b, D2_b^T = L~_{b+2,b} B_b stored [t][r] (zero
+// where the neighbour block is absent).
 __global__ void __launch_bounds__(1024) k_block_couplings(const double* __restrict__ LBall,
                                                         const double* __restrict__ Binv_all,
                                                         int n, int bw, int64_t fstride, int nblk,
-                                                        double* __restrict__ Cf_all,
-                                                        double* __restrict__ Db_all) {
-  __shared__ double Bs[kB][kB + 1], O0[kB][kB + 1], O1[kB][kB + 1];
+                                                        double* __restrict__ C1_all,
+                                                        double* __restrict__ C2_all,
+                                                        double* __restrict__ D1_all,
+                                                        double* __restrict__ D2_all) {
+  __shared__ double Bs[kB][kB + 1], O[kB][kB + 1];
   const int b = blockIdx.x, f = blockIdx.y;
   const int r = threadIdx.y, c = threadIdx.x;
   const double* LB = LBall + f * fstride;
   const int64_t bo = ((int64_t)f * nblk + b) * kB * kB;
   const int W = bw + 1;
   Bs[r][c] = Binv_all[bo + r * kB + c];
-  // Off_blk[m][c] = L~(32 blk + m, 32 (blk - 1) + c)
-  auto off = [&](int blk, int m, int cc) -> double {
-    if (blk < 1 || blk >= nblk) return 0.0;
-    const int i = blk * kB + m, col = (blk - 1) * kB + cc;
+  // L~(32 bi + m, 32 bj + cc), zero outside the matrix and the band
+  auto blk = [&](int bi, int bj, int m, int cc) -> double {
+    if (bi < 0 || bi >= nblk || bj < 0) return 0.0;
+    const int i = bi * kB + m, col = bj * kB + cc;
     if (i >= n || i - col > bw) return 0.0;
     return LB[(int64_t)i * W + (col - i + bw)];
   };
-  O0[r][c] = off(b, r, c);
-  O1[r][c] = off(b + 1, r, c);
-  __syncthreads();
-  double cf = 0.0, db = 0.0;
+  double* outs[4] = {C1_all, C2_all, D1_all, D2_all};
+  for (int which = 0; which < 4; ++which) {
+    __syncthreads();
+    if (which == 0) O[r][c] = blk(b, b - 1, r, c);        // L~_{b,b-1}
+    else if (which == 1) O[r][c] = blk(b, b - 2, r, c);   // L~_{b,b-2}
+    else if (which == 2) O[r][c] = blk(b + 1, b, r, c);   // L~_{b+1,b}
+    else O[r][c] = blk(b + 2, b, r, c);                   // L~_{b+2,b}
+    __syncthreads();
+    double acc = 0.0;
+    if (which < 2) {
 #pragma unroll 8
-  for (int m = 0; m < kB; ++m) {
-    cf = fma(Bs[r][m], O0[m][c], cf);
-    db = fma(O1[r][m], Bs[m][c], db);
+      for (int m = 0; m < kB; ++m) acc = fma(Bs[r][m], O[m][c], acc);   // B_b O
+    } else {
+#pragma unroll 8
+      for (int m = 0; m < kB; ++m) acc = fma(O[r][m], Bs[m][c], acc);   // O B_b
+    }
+    outs[which][bo + r * kB + c] = acc;
   }
-  Cf_all[bo + r * kB + c] = cf;
-  Db_all[bo + r * kB + c] = db;
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -751,12 +851,12 @@ int cluster_max_active(int CL, int n) {
 }
 
 int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
-                    double* Cf, double* Db, cudaStream_t st) {
+                    double* C1, double* C2, double* D1, double* D2, cudaStream_t st) {
   const int nblk = (m.n_free + kB - 1) / kB;
   const int64_t fstride = (int64_t)m.n_free * (m.bw + 1);
   if (n_fac <= 0) return MQS_OK;
   k_block_couplings<<<dim3((unsigned)nblk, (unsigned)n_fac), dim3(kB, kB), 0, st>>>(
-      LB, Binv, m.n_free, m.bw, fstride, nblk, Cf, Db);
+      LB, Binv, m.n_free, m.bw, fstride, nblk, C1, C2, D1, D2);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

@@ -158,8 +158,11 @@ struct DirectLane {
   const double* LB;        // this lane's band Cholesky factor [n][bw+1]
   const double* invd;      // its reciprocal diagonal [n]
   const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
-  const double* Cf;        // block couplings B_b L~_{b,b-1} [n/32][32][32] (cluster kernels)
-  const double* Db;        // block couplings L~_{b+1,b} B_b [n/32][32][32] (cluster kernels)
+  // block couplings of the cluster kernels, [n/32][32][32] each:
+  const double* C1;        // B_b L~_{b,b-1}   [b][r][t]
+  const double* C2;        // B_b L~_{b,b-2}   [b][r][t]
+  const double* D1;        // L~_{b+1,b} B_b   [b][t][r]
+  const double* D2;        // L~_{b+2,b} B_b   [b][t][r]
   const float* LBf;        // FP32 factor, reciprocal diagonal and block inverses (mixed)
   const float* invdf;
   const float* Binvf;
@@ -212,7 +215,7 @@ int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectCons
 // mqs_cluster.cu: FP64 stepping with the block solve spread over warps and a
 // lane split over a cluster of `cluster` CTAs (work vector in shared memory)
 int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
-                    double* Cf, double* Db, cudaStream_t st);
+                    double* C1, double* C2, double* D1, double* D2, cudaStream_t st);
 int cluster_max_n();
 int cluster_max_active(int CL, int n);
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
