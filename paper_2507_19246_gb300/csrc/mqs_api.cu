@@ -124,6 +124,10 @@ struct Batch {
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // side stream for work that overlaps the main stream (Parareal: the fine
+  // factorisation runs beside the coarse one and the first coarse sweep)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int n_sm = 1;
   std::vector<std::unique_ptr<MeshDev>> meshes;
   std::vector<std::unique_ptr<Batch>> batches;
@@ -139,7 +143,28 @@ struct Ctx {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
       }
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
   }
+};
+
+int ensure_side(Ctx& c) {
+  if (!c.side) MQS_CUDA_TRY(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
+  if (!c.ev_fork) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+  if (!c.ev_join) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+  return MQS_OK;
+}
+
+// Work issued while one of these is alive goes to the context's side stream.
+struct OnSide {
+  Ctx& c;
+  cudaStream_t saved;
+  explicit OnSide(Ctx& c_) : c(c_), saved(c_.stream) { c.stream = c.side; }
+  ~OnSide() { c.stream = saved; }
 };
 
 // Record the start (begin = true) or end event of a launch of kind k.
@@ -605,15 +630,18 @@ int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
 }
 
 // Cluster size of the FP64 stepping kernels with the work vector in shared
-// memory: the widest split (8, 4, 2, 1 CTAs per lane) whose clusters are all
-// resident at once; 0 selects the one-CTA kernels (mixed precision, work
-// vector in L2).  env MQS_DIRECT_CLUSTER=0/1/2/4/8 forces a choice.
-int direct_cluster(const MeshDev& m, int lanes, const DirectConst& kc) {
+// memory; 0 selects the one-CTA kernels of mqs_direct.cu (mixed precision,
+// work vector in L2).  The widest split (8, 4, 2 CTAs per lane) whose clusters
+// all fit the SMs in one wave, else 1.  Measured on the 20k-node annulus: one
+// lane (the coarse sweep) steps fastest on 8 CTAs; 64 lanes (the fine batch)
+// on 2 CTAs each, 2.3x faster than on one.  env MQS_DIRECT_CLUSTER=0/1/2/4/8
+// forces a choice.
+int direct_cluster(const MeshDev& m, int lanes, int n_sm, const DirectConst& kc) {
   if (kc.mixed || !kc.w_in_smem || m.n_free > cluster_max_n()) return 0;
   const int forced = env_int("MQS_DIRECT_CLUSTER", -1);
   if (forced == 0 || forced == 1 || forced == 2 || forced == 4 || forced == 8) return forced;
   for (int cl : {8, 4, 2})
-    if (lanes <= cluster_max_active(cl, m.n_free)) return cl;
+    if (lanes * cl <= n_sm && lanes <= cluster_max_active(cl, m.n_free)) return cl;
   return 1;
 }
 
@@ -642,7 +670,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, 
   kc.mixed = mixed ? 1 : 0;
   kc.tol2 = tol * tol;
   kc.max_sweeps = max_sweeps;
-  kc.cluster = direct_cluster(m, lanes, kc);
+  kc.cluster = direct_cluster(m, lanes, n_sm, kc);
   return kc;
 }
 
@@ -735,9 +763,13 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet* ff, in
   return MQS_OK;
 }
 
+// fine_ready: event after which fF is complete (the fine factorisation ran on
+// the side stream), waited for before the first fine batch; null if fF is
+// already ordered on the main stream.
 int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
                         FactorSet& fC, int n_steps, int M, int cf, int max_iters, double tol,
-                        bool mixed, double ir_tol, int max_sweeps, int& iters_out) {
+                        bool mixed, double ir_tol, int max_sweeps, int& iters_out,
+                        cudaEvent_t fine_ready) {
   const cudaStream_t st = ctx->c.stream;
   const int S = n_steps / M, Sc = S / cf, ns = b.n, n = m.n_free;
   const int lanes = ns * M;
@@ -757,7 +789,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
   MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
   const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
   const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
-  if (kc.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fF));
+  if (kc.cluster && !fine_ready) MQS_TRY(ensure_couplings(ctx, b, m, fF));
   if (kchain.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fC));
   auto fine = [&](const DirectSet& d, int nl) -> int {
     return kc.cluster ? launch_cluster(d.desc.as<DirectLane>(), nl, kc, st)
@@ -805,6 +837,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
       }
     fine_steps += (double)dp.host.size() * S;
     exec_steps += (double)dp.host.size() * S;
+    if (k == 1 && fine_ready) MQS_CUDA_TRY(cudaStreamWaitEvent(st, fine_ready, 0));
     MQS_TRY(upload_direct(ctx, dp));
     MQS_TRY(prof_mark(ctx->c, 0, true));
     MQS_TRY(fine(dp, (int)dp.host.size()));
@@ -1176,8 +1209,28 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
       set_error("the banded solver needs n_free * (bw + 1) < 2^31");
       return MQS_EINVAL;
     }
-    FactorSet* ff = factor_set(ctx, b, m, dt_level, mixed, rc);
-    if (!ff) return rc;
+    FactorSet* ff = nullptr;
+    cudaEvent_t fine_ready = nullptr;
+    if (n_slices > 1) {
+      // the fine factor (and its block couplings) on the side stream, beside
+      // the coarse factorisation and the first coarse sweep
+      MQS_TRY(ensure_side(ctx->c));
+      MQS_CUDA_TRY(cudaEventRecord(ctx->c.ev_fork, ctx->c.stream));
+      MQS_CUDA_TRY(cudaStreamWaitEvent(ctx->c.side, ctx->c.ev_fork, 0));
+      {
+        OnSide on(ctx->c);
+        ff = factor_set(ctx, b, m, dt_level, mixed, rc);
+        if (!ff) return rc;
+        const DirectConst kc = direct_const(m, b, b.n * n_slices, ctx->c.n_sm, mixed, cg_tol,
+                                            cg_max_iters);
+        if (kc.cluster) MQS_TRY(ensure_couplings(ctx, b, m, *ff));
+        MQS_CUDA_TRY(cudaEventRecord(ctx->c.ev_join, ctx->c.side));
+      }
+      fine_ready = ctx->c.ev_join;
+    } else {
+      ff = factor_set(ctx, b, m, dt_level, mixed, rc);
+      if (!ff) return rc;
+    }
     FactorSet* fc = nullptr;
     if (dt_prev > 0.0 && !(fc = factor_set(ctx, b, m, dt_prev, mixed, rc))) return rc;
     b.level = level;
@@ -1201,7 +1254,7 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
       if (!fC) return rc;
       MQS_TRY(run_parareal_direct(ctx, b, m, *ff, *fC, nsf, n_slices, coarse_factor,
                                   max_par_iters, par_tol, mixed, cg_tol, cg_max_iters,
-                                  par_iters));
+                                  par_iters, fine_ready));
       b.mode = 4;
       b.M = n_slices;
       MQS_TRY(finish_qoi(b.dpar.qraw.as<double>(), fc ? b.dplain.qraw.as<double>() : nullptr,

@@ -19,11 +19,12 @@
 //                         D1_b = B_b^T L~_{b+1,b}^T, D2_b = B_b^T L~_{b+2,b}^T,
 //                         Q_b = sum_{k >= b+3} L~_kb^T u_k
 // The couplings are precomputed with the factor.  Warp roles: GEMV warps form
-// s_b = w_b - P_b (or y_b - Q_b) for the block solved two rounds later; the
-// solve warps form pre_b = B_b s_b - C2_b y_{b-2} one round ahead, so that the
-// critical path of a round is only v_b = pre_b - C1_b y_{b-1} and its
-// exchange.  The two warp groups hand data over through release/acquire
-// progress counters in shared memory, never through a CTA-wide barrier.
+// s_b = w_b - P_b (or y_b - Q_b) for the block solved two rounds later; pre
+// warps form pre_b = B_b s_b - C2_b y_{b-2} one round ahead; exchange warps
+// (alone on their SM sub-partitions) gather the last block, form
+// v_b = pre_b - C1_b y_{b-1} and send it, which is the whole critical path of
+// a round.  The warp groups hand data over through release/acquire progress
+// counters in shared memory, never through a CTA-wide barrier.
 //
 // Cluster split: every CTA keeps a full copy of the permuted work vector in
 // shared memory and owns rows q*R .. q*R+R-1 (R = 32/CL) of every block, in
@@ -56,6 +57,7 @@ constexpr int kSW = 4;       // solve warps (warps 0..3, one per SM sub-partitio
 constexpr int kPF = 24;      // band values prefetched per GEMV lane (registers)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 20;   // mbarrier polls before a wait gives up
+constexpr int kSpinLimit = 1 << 24;   // progress-counter polls before a wait gives up
 // bytes of block-solve shares a CTA receives from the other CTAs per round
 template <int CL>
 constexpr uint32_t kShareTx = (CL - 1) * kB * sizeof(double);
@@ -63,26 +65,29 @@ constexpr double kPi = 3.14159265358979323846;
 
 template <int CL>
 struct Split {
-  static constexpr int R = kB / CL;              // own rows per block
-  static constexpr int GW = CL <= 2 ? 8 : 4;     // GEMV warps (warps kSW .. kSW+GW-1)
-  static constexpr int H = 4 * GW / R;           // forward: chunks per own row, 8 lanes each
-  static constexpr int TB = R / GW;              // backward: own columns per GEMV warp
-  static constexpr int KG = 32 / TB;             // backward: row groups per own column
-  static constexpr int TPL = (R + 3) / 4;        // own rows per solve lane
-  static constexpr int LV = R >= 4 ? 2 : (R == 2 ? 1 : 0);   // solve reduction levels
-  static_assert(R * H == 4 * GW && H <= 4, "forward items fill the GEMV warps, rows stay in a warp");
+  static constexpr int R = kB / CL;                     // own rows per block
+  static constexpr int GW = CL == 1 ? 8 : (CL == 8 ? 2 : 4);   // GEMV warps
+  static constexpr int GW0 = GW == 2 ? 6 : 4;           // first GEMV warp
+  static constexpr int H = 4 * GW / R;                  // forward: chunks per own row, 8 lanes each
+  static constexpr int TB = R / GW;                     // backward: own columns per GEMV warp
+  static constexpr int KG = 32 / TB;                    // backward: row groups per own column
+  static constexpr int TPX = (R + 1) / 2;               // own rows per exchange / pre lane
+  static constexpr bool PF_C2 = 2 * TPX <= kPF;         // pre lanes prefetch both operands
+  static_assert(R * H == 4 * GW && H >= 1 && H <= 4, "forward items fill the GEMV warps");
   static_assert(TB >= 1 && TB * GW == R, "backward columns fill the GEMV warps");
-  static_assert(kSW + GW <= kNW, "warp roles");
-  static_assert(3 * TPL <= kPF, "solve prefetch fits the register array");
+  static_assert(GW0 + GW <= kNW && GW0 >= 4, "warp roles");
+  static_assert(TPX <= kPF, "exchange prefetch fits the register array");
 };
 
 template <int CL>
 struct CSmem {
   double V[2][CL][kB];                       // block-solve shares [round parity][rank][row]
   double s[4][Split<CL>::R];                 // own rows' s of the block solves, ring by round
+  double pre[2][kB];                         // pre of the block solves, by round parity
   unsigned long long mbar[2];                // share arrivals of V[0], V[1]
   int ydone;                                 // rounds whose solved block is in the copy
   int sdone;                                 // rounds whose s is in the ring
+  int pdone;                                 // rounds whose pre is in shared memory
   int err;                                   // a wait ran out
   double red[kNW];
   double cred[CL][2];                        // per-rank partial sums for cluster reductions
@@ -149,13 +154,13 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Wait until a progress counter reaches target, at most kWaitLimit polls.
+// Wait until a progress counter reaches target, at most kSpinLimit polls.
+// The hand-offs inside a CTA take microseconds, so the wait spins (a sleep
+// between polls costs far more than it saves).
 __device__ __forceinline__ void wait_count(const int* p, int target, int* err) {
   if (*reinterpret_cast<volatile int*>(err)) return;
-  for (int it = 0; it < kWaitLimit; ++it) {
+  for (int it = 0; it < kSpinLimit; ++it)
     if (ld_acquire(p) >= target) return;
-    __nanosleep(32);
-  }
   *reinterpret_cast<volatile int*>(err) = 1;
 }
 
@@ -234,7 +239,7 @@ struct Subst {
   int warp, lane;
   int f_t, f_h, f_g;     // forward GEMV item: own row, chunk, lane in chunk
   int b_t, b_kg, gw;     // backward GEMV: own column, row group; GEMV warp index
-  int s_r, s_g;          // solve lane: block row, term group
+  int x_r, x_g;          // exchange / pre lane: block row, term group (own rows t = x_g + 2k)
   int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
 
   __device__ Subst(const DirectLane& D, double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
@@ -242,19 +247,20 @@ struct Subst {
         bw(bw_), W(bw_ + 1), nblk((n_ + kB - 1) / kB), q(q_) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
-    gw = warp - kSW;
+    gw = warp - S::GW0;
     const int item = gw * 4 + (lane >> 3);
     f_t = item / S::H;
     f_h = item % S::H;
     f_g = lane & 7;
     b_t = gw * S::TB + lane % S::TB;
     b_kg = lane / S::TB;
-    s_r = warp * 8 + (lane & 7);
-    s_g = lane >> 3;
+    x_r = (warp & 1) * 16 + (lane & 15);
+    x_g = lane >> 4;
   }
 
-  __device__ bool is_solve() const { return warp < kSW; }
-  __device__ bool is_gemv() const { return warp >= kSW && warp < kSW + S::GW; }
+  __device__ bool is_exch() const { return warp < 2; }
+  __device__ bool is_pre() const { return warp == 2 || warp == 3; }
+  __device__ bool is_gemv() const { return warp >= S::GW0 && warp < S::GW0 + S::GW; }
   __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
   // own row t of block blk from the copy (0 past n)
   __device__ double own_val(int blk, int t) const {
@@ -350,49 +356,88 @@ struct Subst {
     }
   }
 
-  // Solve-lane operands: pf[3k] coupling to the last block (round g),
-  // pf[3k+1] B entry and pf[3k+2] coupling two blocks back (round g + 1),
-  // own row t = s_g + 4k.
-  __device__ void solve_load(int g, double (&pf)[kPF]) const {
+  // Exchange-lane operand of round g: the coupling to the block solved in
+  // round g - 1 (C1, forward; D1^T, backward), own row t = x_g + 2k.
+  __device__ void x_load(int g, double (&pf)[kPF]) const {
     const int G = 2 * nblk;
 #pragma unroll
-    for (int k = 0; k < S::TPL; ++k) {
-      const int t = s_g + 4 * k;
-      double c1 = 0.0, bv = 0.0, c2 = 0.0;
-      if (t < S::R) {
-        const int tc = q * S::R + t;
-        if (g < G) {
-          const int b = block_of(g);
-          const int64_t o = (int64_t)b * kB * kB;
-          if (g < nblk) {
-            if (b >= 1) c1 = __ldg(C1 + o + s_r * kB + tc);
-          } else if (g >= nblk + 1) {
-            c1 = __ldg(D1 + o + tc * kB + s_r);
-          }
-        }
-        const int g1 = g + 1;
-        if (g1 < G && g1 != nblk) {
-          const int b1 = block_of(g1);
-          const int64_t o = (int64_t)b1 * kB * kB;
-          if (g1 < nblk) {
-            bv = __ldg(Binv + o + s_r * kB + tc);
-            if (b1 >= 2) c2 = __ldg(C2 + o + s_r * kB + tc);
-          } else {
-            bv = __ldg(Binv + o + tc * kB + s_r);
-            if (b1 + 2 < nblk) c2 = __ldg(D2 + o + tc * kB + s_r);
-          }
+    for (int k = 0; k < S::TPX; ++k) {
+      const int t = x_g + 2 * k;
+      double c = 0.0;
+      if (t < S::R && g < G) {
+        const int b = block_of(g), tc = q * S::R + t;
+        const int64_t o = (int64_t)b * kB * kB;
+        if (g < nblk) {
+          if (b >= 1) c = __ldg(C1 + o + x_r * kB + tc);
+        } else if (g >= nblk + 1) {
+          c = __ldg(D1 + o + tc * kB + x_r);
         }
       }
-      pf[3 * k] = c1;
-      pf[3 * k + 1] = bv;
-      pf[3 * k + 2] = c2;
+      pf[k] = c;
     }
   }
 
-  __device__ double reduce_terms(double v) const {
-    if (S::LV >= 1) v += __shfl_xor_sync(kFull, v, 8);
-    if (S::LV >= 2) v += __shfl_xor_sync(kFull, v, 16);
-    return v;
+  // Pre-lane operands of round g1: pf[k] the B entry, pf[TPX + k] the
+  // coupling two blocks back (C2, forward; D2^T, backward).
+  __device__ void p_load(int g1, double (&pf)[kPF]) const {
+    const int G = 2 * nblk;
+#pragma unroll
+    for (int k = 0; k < S::TPX; ++k) {
+      const int t = x_g + 2 * k;
+      double bv = 0.0, c2 = 0.0;
+      if (t < S::R && g1 < G) {
+        const int b1 = block_of(g1), tc = q * S::R + t;
+        const int64_t o = (int64_t)b1 * kB * kB;
+        if (g1 < nblk) {
+          bv = __ldg(Binv + o + x_r * kB + tc);
+          if (S::PF_C2 && b1 >= 2) c2 = __ldg(C2 + o + x_r * kB + tc);
+        } else {
+          bv = __ldg(Binv + o + tc * kB + x_r);
+          if (S::PF_C2 && g1 >= nblk + 2) c2 = __ldg(D2 + o + tc * kB + x_r);
+        }
+      }
+      pf[k] = bv;
+      if (S::PF_C2) pf[S::TPX + k] = c2;
+    }
+  }
+
+  // pre of round g1 (lane partial over its own rows): B s - C2 y_{b-2}
+  // (forward) or B^T s - D2^T u_{b+2} (backward); the first backward round
+  // takes s = y_b (no band part, no couplings).
+  __device__ double pre_of(int g1, const double (&pf)[kPF]) const {
+    const int b1 = block_of(g1);
+    double p0 = 0.0, p1 = 0.0;
+    if (g1 == nblk) {
+#pragma unroll
+      for (int k = 0; k < S::TPX; ++k) {
+        const int t = x_g + 2 * k;
+        if (t < S::R) p0 = fma(pf[k], own_val(b1, t), p0);
+      }
+      return p0;
+    }
+    const bool fwd = g1 < nblk;
+    const bool two = fwd ? b1 >= 2 : g1 >= nblk + 2;
+    const int bb = block_of(g1 - 2);
+    const double* s1 = sm.s[g1 & 3];
+#pragma unroll
+    for (int k = 0; k < S::TPX; ++k) {
+      const int t = x_g + 2 * k;
+      if (t < S::R) {
+        p0 = fma(pf[k], s1[t], p0);
+        if (two) {
+          double c2;
+          if constexpr (S::PF_C2) {
+            c2 = pf[S::TPX + k];
+          } else {
+            const int64_t o = (int64_t)b1 * kB * kB;
+            const int tc = q * S::R + t;
+            c2 = fwd ? __ldg(C2 + o + x_r * kB + tc) : __ldg(D2 + o + tc * kB + x_r);
+          }
+          p1 = fma(-c2, own_val(bb, t), p1);
+        }
+      }
+    }
+    return p0 + p1;
   }
 
   // Forward then backward substitution; on return w holds u (all rows).
@@ -401,11 +446,12 @@ struct Subst {
     if (threadIdx.x == 0) {
       sm.ydone = -1;
       sm.sdone = -1;
+      sm.pdone = -1;
     }
     __syncthreads();
     if (is_gemv()) {
       // s of rounds 0 and 1: own right-hand sides (no band part yet)
-      const int gt = threadIdx.x - kSW * 32;
+      const int gt = threadIdx.x - S::GW0 * 32;
       for (int j = 0; j < 2; ++j)
         if (j < G && j != nblk && gt < S::R) {
           const int row = j * kB + q * S::R + gt;
@@ -427,16 +473,24 @@ struct Subst {
         group_sync(2, S::GW * 32);
         if (gt == 0) st_release(&sm.sdone, j);
       }
-    } else if (is_solve()) {
-      // pre of round 0: B_0 s_0
-      wait_count(&sm.sdone, 0, &sm.err);
-      double pre = 0.0;
-#pragma unroll
-      for (int k = 0; k < S::TPL; ++k) {
-        const int t = s_g + 4 * k;
-        if (t < S::R) pre = fma(__ldg(Binv + s_r * kB + q * S::R + t), sm.s[0][t], pre);
+    } else if (is_pre()) {
+      // pre of every round, one round ahead of the exchange warps
+      for (int g1 = 0; g1 < G; ++g1) {
+        p_load(g1, pf);
+        if (g1 == nblk) {
+          wait_count(&sm.ydone, nblk, &sm.err);          // y of the last forward block
+        } else {
+          wait_count(&sm.ydone, g1 - 1, &sm.err);        // the block two rounds back
+          wait_count(&sm.sdone, g1, &sm.err);
+        }
+        double v = pre_of(g1, pf);
+        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 16);
+        if (x_g == 0) sm.pre[g1 & 1][x_r] = v;
+        group_sync(3, 64);
+        if (threadIdx.x == 64) st_release(&sm.pdone, g1);
       }
-      solve_load(0, pf);
+    } else if (is_exch()) {
+      x_load(0, pf);
       for (int g = 0; g <= G; ++g) {
         // [A] the shares of round g - 1 into the copy
         if (CL > 1 && g >= 1) {
@@ -446,71 +500,45 @@ struct Subst {
           mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
           if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
           const double* Vb = &sm.V[(g - 1) & 1][0][0];
-          double acc = s_g < CL ? Vb[s_g * kB + s_r] : 0.0;
-          for (int p = s_g + 4; p < CL; p += 4) acc += Vb[p * kB + s_r];
-          if (CL > 1) acc += __shfl_xor_sync(kFull, acc, 8);
-          if (CL > 2) acc += __shfl_xor_sync(kFull, acc, 16);
-          const int row = bp * kB + s_r;
-          if (s_g == 0 && row < n) w[row] = acc;
+          double acc = x_g < CL ? Vb[x_g * kB + x_r] : 0.0;
+          for (int p = x_g + 2; p < CL; p += 2) acc += Vb[p * kB + x_r];
+          acc += __shfl_xor_sync(kFull, acc, 16);
+          const int row = bp * kB + x_r;
+          if (x_g == 0 && row < n) w[row] = acc;
         }
         if (g == G) break;
-        group_sync(1, kSW * 32);
+        group_sync(1, 64);
         if (threadIdx.x == 0) st_release(&sm.ydone, g);
         const bool fwd = g < nblk;
         const int b = block_of(g);
-        // [B] first backward block: pre = B_b^T y_b (no band part, no couplings)
-        if (g == nblk) {
-          pre = 0.0;
-#pragma unroll
-          for (int k = 0; k < S::TPL; ++k) {
-            const int t = s_g + 4 * k;
-            if (t < S::R)
-              pre = fma(__ldg(Binv + (int64_t)b * kB * kB + (q * S::R + t) * kB + s_r),
-                        own_val(b, t), pre);
-          }
-        }
-        // [C] v = pre - C1 y_{b-1} (forward) or pre - D1 u_{b+1} (backward)
+        // [C] v = pre - C1 y_{b-1} (forward) or pre - D1^T u_{b+1} (backward)
         const bool c1 = fwd ? b >= 1 : g >= nblk + 1;
         const int bp = block_of(g - 1);
-        double y1[S::TPL];
-        double v0 = pre, v1 = 0.0;
+        wait_count(&sm.pdone, g, &sm.err);
+        double v0 = x_g == 0 ? sm.pre[g & 1][x_r] : 0.0, v1 = 0.0;
+        if (c1) {
 #pragma unroll
-        for (int k = 0; k < S::TPL; ++k) {
-          const int t = s_g + 4 * k;
-          y1[k] = (c1 && t < S::R) ? own_val(bp, t) : 0.0;
-          if (t < S::R) v1 = fma(-pf[3 * k], y1[k], v1);
+          for (int k = 0; k < S::TPX; ++k) {
+            const int t = x_g + 2 * k;
+            if (t < S::R) v1 = fma(-pf[k], own_val(bp, t), v1);
+          }
         }
-        const double v = reduce_terms(v0 + v1);
+        double v = v0 + v1;
+        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 16);
         if constexpr (CL == 1) {
-          const int row = b * kB + s_r;
-          if (s_g == 0 && row < n) w[row] = v;
+          const int row = b * kB + x_r;
+          if (x_g == 0 && row < n) w[row] = v;
         } else {
-          const uint32_t la = smem_addr(&sm.V[g & 1][q][s_r]);
+          const uint32_t la = smem_addr(&sm.V[g & 1][q][x_r]);
           const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
-          for (int p = s_g; p < CL; p += 4) {
+          for (int p = x_g; p < CL; p += 2) {
             if (p == q)
-              sm.V[g & 1][q][s_r] = v;   // own share: ordered by the group barrier of the next round
+              sm.V[g & 1][q][x_r] = v;   // own share: ordered by the group barrier of the next round
             else
               st_async(map_rank(la, p), v, map_rank(lm, p));
           }
         }
-        // [D] pre of round g + 1: B s - C2 y_{b'-2} (forward) or B^T s - D2 u_{b'+2}
-        const int g1 = g + 1;
-        if (g1 < G && g1 != nblk) {
-          wait_count(&sm.sdone, g1, &sm.err);
-          const double* s1 = sm.s[g1 & 3];
-          double p0 = 0.0, p1 = 0.0;
-#pragma unroll
-          for (int k = 0; k < S::TPL; ++k) {
-            const int t = s_g + 4 * k;
-            if (t < S::R) {
-              p0 = fma(pf[3 * k + 1], s1[t], p0);
-              p1 = fma(-pf[3 * k + 2], y1[k], p1);   // two blocks back = this round's last block
-            }
-          }
-          pre = p0 + p1;
-        }
-        solve_load(g + 1, pf);
+        x_load(g + 1, pf);
       }
     }
     __syncthreads();
@@ -530,13 +558,16 @@ struct Own {
   }
 };
 
-// mbarriers of the share exchange: initialised once, each armed one round
-// ahead (rounds 0 and 1 here, round r + 2 when round r's shares are consumed).
+// Error flag cleared; mbarriers of the share exchange (CL > 1) initialised
+// once, each armed one round ahead (rounds 0 and 1 here, round r + 2 when
+// round r's shares are consumed).
 template <int CL>
 __device__ void cluster_setup(CSmem<CL>& sm) {
-  if constexpr (CL > 1) {
+  if (threadIdx.x == 0) sm.err = 0;
+  if constexpr (CL == 1) {
+    __syncthreads();
+  } else {
     if (threadIdx.x == 0) {
-      sm.err = 0;
       for (int x = 0; x < 2; ++x) {
         const uint32_t mb = smem_addr(&sm.mbar[x]);
         mbar_init(mb);
@@ -548,14 +579,16 @@ __device__ void cluster_setup(CSmem<CL>& sm) {
   }
 }
 
-// No CTA leaves while shares may still be sent to it; a timed-out wait is
-// reported on the lane's status.
+// No CTA leaves while shares may still be sent to it; a timed-out wait (of
+// any cluster size) is reported on the lane's status.
 template <int CL>
 __device__ void cluster_finish(CSmem<CL>& sm, const DirectLane& D) {
   if constexpr (CL > 1) {
     cluster_sync_all();
-    if (threadIdx.x == 0 && sm.err && D.status_out) atomicOr(D.status_out, MQS_ST_TIMEOUT);
+  } else {
+    __syncthreads();
   }
+  if (threadIdx.x == 0 && sm.err && D.status_out) atomicOr(D.status_out, MQS_ST_TIMEOUT);
 }
 
 // Advance one lane by n_steps steps.  a_init: initial state (all nodes
