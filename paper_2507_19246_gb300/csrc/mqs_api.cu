@@ -43,7 +43,7 @@ struct FactorSet {
   double dt = 0.0;
   bool have64 = false, have32 = false, have_cpl = false;
   DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
-  DevBuf C1, C2, D1, D2;        // [samples][n/32][32][32] block couplings (cluster kernels)
+  DevBuf B64, C1, C2, D1, D2;   // [samples][n/64][64][64] block inverses and couplings (cluster kernels)
   DevBuf LBf, invdf, Binvf;     // FP32 factor (mixed precision)
 };
 
@@ -617,14 +617,20 @@ FactorSet* factor_set(mqs_ctx* ctx, Batch& b, const MeshDev& m, double dt, bool 
   return rc == MQS_OK ? f : nullptr;
 }
 
-// Block couplings of an FP64 factor set, for the cluster stepping kernels.
+// Elements per factor of each block array of the cluster kernels.
+size_t cluster_bstride(const MeshDev& m) {
+  const size_t kb = (size_t)cluster_block_rows();
+  return ((size_t)m.n_free + kb - 1) / kb * kb * kb;
+}
+
+// Block inverses and couplings of an FP64 factor set, for the cluster stepping kernels.
 int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
   if (f.have_cpl) return MQS_OK;
-  const size_t bstride = (size_t)block_count(m.n_free) * 32 * 32;
-  for (DevBuf* x : {&f.C1, &f.C2, &f.D1, &f.D2})
+  const size_t bstride = cluster_bstride(m);
+  for (DevBuf* x : {&f.B64, &f.C1, &f.C2, &f.D1, &f.D2})
     MQS_TRY(x->ensure(bstride * b.n * sizeof(double)));
-  MQS_TRY(block_couplings(m, b.n, f.LB.as<double>(), f.Binv.as<double>(), f.C1.as<double>(),
-                          f.C2.as<double>(), f.D1.as<double>(), f.D2.as<double>(), ctx->c.stream));
+  MQS_TRY(block_prep(m, b.n, f.LB.as<double>(), f.B64.as<double>(), f.C1.as<double>(),
+                     f.C2.as<double>(), f.D1.as<double>(), f.D2.as<double>(), ctx->c.stream));
   f.have_cpl = true;
   return MQS_OK;
 }
@@ -684,7 +690,8 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   d.LB = f.LB.as<double>() + fstride * sample;
   d.invd = f.invd.as<double>() + (size_t)m.n_free * sample;
   d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
-  const size_t bo = (size_t)block_count(m.n_free) * 32 * 32 * sample;
+  const size_t bo = cluster_bstride(m) * sample;
+  d.B64 = f.B64.as<double>() + bo;
   d.C1 = f.C1.as<double>() + bo;
   d.C2 = f.C2.as<double>() + bo;
   d.D1 = f.D1.as<double>() + bo;

@@ -50,11 +50,10 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kB = 32;       // rows per substitution block
+constexpr int kB = 64;       // rows per substitution block (one exchange round per block)
 constexpr int kNT = 512;     // threads per CTA
 constexpr int kNW = kNT / 32;
-constexpr int kSW = 4;       // solve warps (warps 0..3, one per SM sub-partition)
-constexpr int kPF = 24;      // band values prefetched per GEMV lane (registers)
+constexpr int kPF = 24;      // values prefetched per lane (registers)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 20;   // mbarrier polls before a wait gives up
 constexpr int kSpinLimit = 1 << 24;   // progress-counter polls before a wait gives up
@@ -63,20 +62,38 @@ template <int CL>
 constexpr uint32_t kShareTx = (CL - 1) * kB * sizeof(double);
 constexpr double kPi = 3.14159265358979323846;
 
+// Warp roles per cluster size (R = 64/CL own rows per block):
+//  * exchange warps X (gather, v = pre - C1 y, send) and pre warps P, each
+//    group covering the 64 rows of a block with RW rows per warp and
+//    LPR = 32/RW lanes per row (own rows t = g + LPR k of a lane; the P group
+//    is wider with 2 CTAs so that a lane's operands fit in registers);
+//  * GEMV warps: forward items of 4 lanes (own row t, chunk h), H chunks
+//    per row inside one warp; backward TB own columns per warp, KG = 32/TB
+//    row groups.
+// With 8 CTAs the exchange warps sit alone on sub-partitions 0 and 1, the pre
+// and GEMV warps share 2 and 3.
 template <int CL>
 struct Split {
-  static constexpr int R = kB / CL;                     // own rows per block
+  static constexpr int R = kB / CL;
+  static constexpr int NX = CL == 8 ? 2 : 4;            // exchange warps
+  static constexpr int NP = CL == 2 ? 8 : NX;           // pre warps
+  static constexpr int RW = kB / NX, LPR = 32 / RW;     // exchange: rows per warp, lanes per row
+  static constexpr int RWP = kB / NP, LPRP = 32 / RWP;  // pre: rows per warp, lanes per row
+  static constexpr int X0 = 0, P0 = NX;                 // first exchange / pre warp
   static constexpr int GW = CL == 1 ? 8 : (CL == 8 ? 2 : 4);   // GEMV warps
-  static constexpr int GW0 = GW == 2 ? 6 : 4;           // first GEMV warp
-  static constexpr int H = 4 * GW / R;                  // forward: chunks per own row, 8 lanes each
-  static constexpr int TB = R / GW;                     // backward: own columns per GEMV warp
-  static constexpr int KG = 32 / TB;                    // backward: row groups per own column
-  static constexpr int TPX = (R + 1) / 2;               // own rows per exchange / pre lane
-  static constexpr bool PF_C2 = 2 * TPX <= kPF;         // pre lanes prefetch both operands
-  static_assert(R * H == 4 * GW && H >= 1 && H <= 4, "forward items fill the GEMV warps");
-  static_assert(TB >= 1 && TB * GW == R, "backward columns fill the GEMV warps");
-  static_assert(GW0 + GW <= kNW && GW0 >= 4, "warp roles");
-  static_assert(TPX <= kPF, "exchange prefetch fits the register array");
+  static constexpr int GW0 = CL == 8 ? 6 : NX + NP;     // first GEMV warp
+  static constexpr int H = 8 * GW / R;                  // forward chunks per own row
+  static constexpr int TB = R / GW;                     // backward own columns per GEMV warp
+  static constexpr int KG = 32 / TB;                    // backward row groups per own column
+  static constexpr int TPX = R / LPR;                   // own rows per exchange lane
+  static constexpr int TPP = R / LPRP;                  // own rows per pre lane
+  static constexpr bool PF_X = TPX <= kPF;              // exchange lanes prefetch C1
+  static constexpr bool PF_B = TPP <= kPF;              // pre lanes prefetch B
+  static constexpr bool PF_C2 = 2 * TPP <= kPF;         // ... and C2
+  static_assert(R * H == 8 * GW && H >= 1 && H <= 8, "forward items fill the GEMV warps");
+  static_assert(TB >= 1 && TB * GW == R && KG >= 1, "backward columns fill the GEMV warps");
+  static_assert(RW * LPR == 32 && R % LPR == 0 && RWP * LPRP == 32 && R % LPRP == 0, "lanes");
+  static_assert(P0 >= X0 + NX && GW0 >= P0 + NP && GW0 + GW <= kNW, "disjoint warp roles");
 };
 
 template <int CL>
@@ -226,8 +243,9 @@ struct GemvDesc {
 template <int CL>
 struct Subst {
   using S = Split<CL>;
+  static constexpr int kBB = kB * kB;
   const double* __restrict__ LB;
-  const double* __restrict__ Binv;
+  const double* __restrict__ B;    // 64 x 64 diagonal-block inverses [b][r][t]
   const double* __restrict__ C1;   // [b][r][t]
   const double* __restrict__ C2;   // [b][r][t]
   const double* __restrict__ D1;   // D1_b^T: [b][t][r]
@@ -239,33 +257,43 @@ struct Subst {
   int warp, lane;
   int f_t, f_h, f_g;     // forward GEMV item: own row, chunk, lane in chunk
   int b_t, b_kg, gw;     // backward GEMV: own column, row group; GEMV warp index
-  int x_r, x_g;          // exchange / pre lane: block row, term group (own rows t = x_g + 2k)
+  int x_r, x_g;          // exchange lane: block row, term group (own rows t = x_g + LPR k)
+  int p_r, p_g;          // pre lane: block row, term group (own rows t = p_g + LPRP k)
   int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
 
   __device__ Subst(const DirectLane& D, double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
-      : LB(D.LB), Binv(D.Binv), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), w(w_), sm(sm_), n(n_),
+      : LB(D.LB), B(D.B64), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), w(w_), sm(sm_), n(n_),
         bw(bw_), W(bw_ + 1), nblk((n_ + kB - 1) / kB), q(q_) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     gw = warp - S::GW0;
-    const int item = gw * 4 + (lane >> 3);
+    const int item = gw * 8 + (lane >> 2);
     f_t = item / S::H;
     f_h = item % S::H;
-    f_g = lane & 7;
+    f_g = lane & 3;
     b_t = gw * S::TB + lane % S::TB;
     b_kg = lane / S::TB;
-    x_r = (warp & 1) * 16 + (lane & 15);
-    x_g = lane >> 4;
+    x_r = (warp - S::X0) * S::RW + lane % S::RW;
+    x_g = lane / S::RW;
+    p_r = (warp - S::P0) * S::RWP + lane % S::RWP;
+    p_g = lane / S::RWP;
   }
 
-  __device__ bool is_exch() const { return warp < 2; }
-  __device__ bool is_pre() const { return warp == 2 || warp == 3; }
+  __device__ bool is_exch() const { return warp >= S::X0 && warp < S::X0 + S::NX; }
+  __device__ bool is_pre() const { return warp >= S::P0 && warp < S::P0 + S::NP; }
   __device__ bool is_gemv() const { return warp >= S::GW0 && warp < S::GW0 + S::GW; }
   __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
   // own row t of block blk from the copy (0 past n)
   __device__ double own_val(int blk, int t) const {
     const int row = blk * kB + q * S::R + t;
     return row < n ? w[row] : 0.0;
+  }
+  // sum over the lanes of a row (lanes of a row differ in the bits above rw)
+  template <int rw>
+  __device__ static double row_sum(double v) {
+#pragma unroll
+    for (int o = rw; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
   }
 
   // GEMV items of round j's s: forward, row i of block j over the columns of
@@ -278,7 +306,7 @@ struct Subst {
       const int i = j * kB + q * S::R + f_t;
       if (i >= n) return d;
       const int lo = max(0, i - bw), hi = (j - 2) * kB;
-      const int c0 = lo + 8 * f_h + f_g, st = 8 * S::H;
+      const int c0 = lo + 4 * f_h + f_g, st = 4 * S::H;
       if (c0 >= hi) return d;
       d.cnt = (hi - c0 + st - 1) / st;
       d.off = (int64_t)i * W + (c0 - i + bw);
@@ -339,9 +367,9 @@ struct Subst {
     if (j < nblk) {
       acc += __shfl_xor_sync(kFull, acc, 1);
       acc += __shfl_xor_sync(kFull, acc, 2);
-      acc += __shfl_xor_sync(kFull, acc, 4);
-      if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 8);
-      if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 16);
+      if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 4);
+      if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 8);
+      if (S::H > 4) acc += __shfl_xor_sync(kFull, acc, 16);
       if (f_g == 0 && f_h == 0) {
         const int row = j * kB + q * S::R + f_t;
         sj[f_t] = row < n ? w[row] - acc : 0.0;
@@ -356,48 +384,39 @@ struct Subst {
     }
   }
 
-  // Exchange-lane operand of round g: the coupling to the block solved in
-  // round g - 1 (C1, forward; D1^T, backward), own row t = x_g + 2k.
-  __device__ void x_load(int g, double (&pf)[kPF]) const {
-    const int G = 2 * nblk;
-#pragma unroll
-    for (int k = 0; k < S::TPX; ++k) {
-      const int t = x_g + 2 * k;
-      double c = 0.0;
-      if (t < S::R && g < G) {
-        const int b = block_of(g), tc = q * S::R + t;
-        const int64_t o = (int64_t)b * kB * kB;
-        if (g < nblk) {
-          if (b >= 1) c = __ldg(C1 + o + x_r * kB + tc);
-        } else if (g >= nblk + 1) {
-          c = __ldg(D1 + o + tc * kB + x_r);
-        }
-      }
-      pf[k] = c;
-    }
+  // coupling of round g to the block of round g - 1 for own row t (C1, forward;
+  // D1^T, backward; 0 where absent)
+  __device__ double c1_val(int g, int t) const {
+    const int b = block_of(g), tc = q * S::R + t;
+    const int64_t o = (int64_t)b * kBB;
+    if (g < nblk) return b >= 1 ? __ldg(C1 + o + x_r * kB + tc) : 0.0;
+    return g >= nblk + 1 ? __ldg(D1 + o + tc * kB + x_r) : 0.0;
+  }
+  __device__ double b_val(int g1, int t) const {
+    const int b1 = block_of(g1), tc = q * S::R + t;
+    const int64_t o = (int64_t)b1 * kBB;
+    return g1 < nblk ? __ldg(B + o + p_r * kB + tc) : __ldg(B + o + tc * kB + p_r);
+  }
+  __device__ double c2_val(int g1, int t) const {
+    const int b1 = block_of(g1), tc = q * S::R + t;
+    const int64_t o = (int64_t)b1 * kBB;
+    if (g1 < nblk) return b1 >= 2 ? __ldg(C2 + o + p_r * kB + tc) : 0.0;
+    return (g1 != nblk && g1 >= nblk + 2) ? __ldg(D2 + o + tc * kB + p_r) : 0.0;
   }
 
-  // Pre-lane operands of round g1: pf[k] the B entry, pf[TPX + k] the
-  // coupling two blocks back (C2, forward; D2^T, backward).
-  __device__ void p_load(int g1, double (&pf)[kPF]) const {
-    const int G = 2 * nblk;
+  __device__ void x_load(int g, double (&pf)[kPF]) const {
+    if constexpr (S::PF_X) {
 #pragma unroll
-    for (int k = 0; k < S::TPX; ++k) {
-      const int t = x_g + 2 * k;
-      double bv = 0.0, c2 = 0.0;
-      if (t < S::R && g1 < G) {
-        const int b1 = block_of(g1), tc = q * S::R + t;
-        const int64_t o = (int64_t)b1 * kB * kB;
-        if (g1 < nblk) {
-          bv = __ldg(Binv + o + x_r * kB + tc);
-          if (S::PF_C2 && b1 >= 2) c2 = __ldg(C2 + o + x_r * kB + tc);
-        } else {
-          bv = __ldg(Binv + o + tc * kB + x_r);
-          if (S::PF_C2 && g1 >= nblk + 2) c2 = __ldg(D2 + o + tc * kB + x_r);
-        }
-      }
-      pf[k] = bv;
-      if (S::PF_C2) pf[S::TPX + k] = c2;
+      for (int k = 0; k < S::TPX; ++k)
+        pf[k] = g < 2 * nblk ? c1_val(g, x_g + S::LPR * k) : 0.0;
+    }
+  }
+  __device__ void p_load(int g1, double (&pf)[kPF]) const {
+#pragma unroll
+    for (int k = 0; k < S::TPP; ++k) {
+      const int t = p_g + S::LPRP * k;
+      if constexpr (S::PF_B) pf[k] = g1 < 2 * nblk ? b_val(g1, t) : 0.0;
+      if constexpr (S::PF_C2) pf[S::TPP + k] = g1 < 2 * nblk ? c2_val(g1, t) : 0.0;
     }
   }
 
@@ -407,34 +426,20 @@ struct Subst {
   __device__ double pre_of(int g1, const double (&pf)[kPF]) const {
     const int b1 = block_of(g1);
     double p0 = 0.0, p1 = 0.0;
-    if (g1 == nblk) {
-#pragma unroll
-      for (int k = 0; k < S::TPX; ++k) {
-        const int t = x_g + 2 * k;
-        if (t < S::R) p0 = fma(pf[k], own_val(b1, t), p0);
-      }
-      return p0;
-    }
-    const bool fwd = g1 < nblk;
-    const bool two = fwd ? b1 >= 2 : g1 >= nblk + 2;
+    const bool first_bwd = g1 == nblk;
+    const bool two = g1 < nblk ? b1 >= 2 : g1 >= nblk + 2;
     const int bb = block_of(g1 - 2);
     const double* s1 = sm.s[g1 & 3];
 #pragma unroll
-    for (int k = 0; k < S::TPX; ++k) {
-      const int t = x_g + 2 * k;
-      if (t < S::R) {
-        p0 = fma(pf[k], s1[t], p0);
-        if (two) {
-          double c2;
-          if constexpr (S::PF_C2) {
-            c2 = pf[S::TPX + k];
-          } else {
-            const int64_t o = (int64_t)b1 * kB * kB;
-            const int tc = q * S::R + t;
-            c2 = fwd ? __ldg(C2 + o + x_r * kB + tc) : __ldg(D2 + o + tc * kB + x_r);
-          }
-          p1 = fma(-c2, own_val(bb, t), p1);
-        }
+    for (int k = 0; k < S::TPP; ++k) {
+      const int t = p_g + S::LPRP * k;
+      double bv;
+      if constexpr (S::PF_B) bv = pf[k]; else bv = b_val(g1, t);
+      p0 = fma(bv, first_bwd ? own_val(b1, t) : s1[t], p0);
+      if (two) {
+        double c2;
+        if constexpr (S::PF_C2) c2 = pf[S::TPP + k]; else c2 = c2_val(g1, t);
+        p1 = fma(-c2, own_val(bb, t), p1);
       }
     }
     return p0 + p1;
@@ -453,10 +458,11 @@ struct Subst {
       // s of rounds 0 and 1: own right-hand sides (no band part yet)
       const int gt = threadIdx.x - S::GW0 * 32;
       for (int j = 0; j < 2; ++j)
-        if (j < G && j != nblk && gt < S::R) {
-          const int row = j * kB + q * S::R + gt;
-          sm.s[j & 3][gt] = row < n ? w[row] : 0.0;
-        }
+        for (int t = gt; t < S::R; t += S::GW * 32)
+          if (j < G && j != nblk) {
+            const int row = j * kB + q * S::R + t;
+            sm.s[j & 3][t] = row < n ? w[row] : 0.0;
+          }
       GemvDesc cur = gemv_desc(2);
       gemv_load(cur, pf);
       group_sync(2, S::GW * 32);
@@ -483,16 +489,15 @@ struct Subst {
           wait_count(&sm.ydone, g1 - 1, &sm.err);        // the block two rounds back
           wait_count(&sm.sdone, g1, &sm.err);
         }
-        double v = pre_of(g1, pf);
-        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 16);
-        if (x_g == 0) sm.pre[g1 & 1][x_r] = v;
-        group_sync(3, 64);
-        if (threadIdx.x == 64) st_release(&sm.pdone, g1);
+        const double v = row_sum<S::RWP>(pre_of(g1, pf));
+        if (p_g == 0) sm.pre[g1 & 1][p_r] = v;
+        group_sync(3, S::NP * 32);
+        if (threadIdx.x == S::P0 * 32) st_release(&sm.pdone, g1);
       }
     } else if (is_exch()) {
       x_load(0, pf);
       for (int g = 0; g <= G; ++g) {
-        // [A] the shares of round g - 1 into the copy
+        // [A] the shares of round g - 1 into the copy (rank order, as a tree)
         if (CL > 1 && g >= 1) {
           const int bp = block_of(g - 1);
           const int64_t r = rounds + g - 1;
@@ -500,15 +505,21 @@ struct Subst {
           mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
           if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
           const double* Vb = &sm.V[(g - 1) & 1][0][0];
-          double acc = x_g < CL ? Vb[x_g * kB + x_r] : 0.0;
-          for (int p = x_g + 2; p < CL; p += 2) acc += Vb[p * kB + x_r];
-          acc += __shfl_xor_sync(kFull, acc, 16);
+          constexpr int NV = CL / S::LPR > 0 ? CL / S::LPR : 1;   // shares summed by this lane
+          double v[NV];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) v[k] = Vb[(x_g + S::LPR * k) * kB + x_r];
+#pragma unroll
+          for (int span = 1; span < NV; span <<= 1)
+#pragma unroll
+            for (int k = 0; k + span < NV; k += 2 * span) v[k] += v[k + span];
+          const double acc = row_sum<S::RW>(v[0]);
           const int row = bp * kB + x_r;
           if (x_g == 0 && row < n) w[row] = acc;
         }
         if (g == G) break;
-        group_sync(1, 64);
-        if (threadIdx.x == 0) st_release(&sm.ydone, g);
+        group_sync(1, S::NX * 32);
+        if (threadIdx.x == S::X0 * 32) st_release(&sm.ydone, g);
         const bool fwd = g < nblk;
         const int b = block_of(g);
         // [C] v = pre - C1 y_{b-1} (forward) or pre - D1^T u_{b+1} (backward)
@@ -519,19 +530,23 @@ struct Subst {
         if (c1) {
 #pragma unroll
           for (int k = 0; k < S::TPX; ++k) {
-            const int t = x_g + 2 * k;
-            if (t < S::R) v1 = fma(-pf[k], own_val(bp, t), v1);
+            const int t = x_g + S::LPR * k;
+            double c;
+            if constexpr (S::PF_X) c = pf[k]; else c = c1_val(g, t);
+            if (k & 1)
+              v1 = fma(-c, own_val(bp, t), v1);
+            else
+              v0 = fma(-c, own_val(bp, t), v0);
           }
         }
-        double v = v0 + v1;
-        if (S::R > 1) v += __shfl_xor_sync(kFull, v, 16);
+        const double v = row_sum<S::RW>(v0 + v1);
         if constexpr (CL == 1) {
           const int row = b * kB + x_r;
           if (x_g == 0 && row < n) w[row] = v;
         } else {
           const uint32_t la = smem_addr(&sm.V[g & 1][q][x_r]);
           const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
-          for (int p = x_g; p < CL; p += 2) {
+          for (int p = x_g; p < CL; p += S::LPR) {
             if (p == q)
               sm.V[g & 1][q][x_r] = v;   // own share: ordered by the group barrier of the next round
             else
@@ -746,48 +761,79 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   cluster_finish<CL>(sm, D);
 }
 
-// ---------------------------------------------------------------- block couplings
-// Per factor and block b: C1_b = B_b L~_{b,b-1}, C2_b = B_b L~_{b,b-2} stored
-// [r][t]; D1_b^T = L~_{b+1,b} B_b, D2_b^T = L~_{b+2,b} B_b stored [t][r] (zero
-// where the neighbour block is absent).
-__global__ void __launch_bounds__(1024) k_block_couplings(const double* __restrict__ LBall,
-                                                        const double* __restrict__ Binv_all,
-                                                        int n, int bw, int64_t fstride, int nblk,
-                                                        double* __restrict__ C1_all,
-                                                        double* __restrict__ C2_all,
-                                                        double* __restrict__ D1_all,
-                                                        double* __restrict__ D2_all) {
-  __shared__ double Bs[kB][kB + 1], O[kB][kB + 1];
-  const int b = blockIdx.x, f = blockIdx.y;
-  const int r = threadIdx.y, c = threadIdx.x;
+// ---------------------------------------------------------------- block preparation
+// One CTA per (64-row block b, factor): the inverse B_b of the unit lower
+// diagonal block of L~ (identity rows past n) by forward substitution, one
+// thread per column, then the couplings as dense products: C1_b = B_b
+// L~_{b,b-1}, C2_b = B_b L~_{b,b-2} stored [r][t]; D1_b^T = L~_{b+1,b} B_b,
+// D2_b^T = L~_{b+2,b} B_b stored [t][r] (zero where the block is absent).
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __restrict__ LBall, int n,
+                                                            int bw, int64_t fstride, int nblk,
+                                                            double* __restrict__ B_all,
+                                                            double* __restrict__ C1_all,
+                                                            double* __restrict__ C2_all,
+                                                            double* __restrict__ D1_all,
+                                                            double* __restrict__ D2_all) {
+  extern __shared__ __align__(16) unsigned char prep_smem[];
+  double (*O)[kB + 1] = reinterpret_cast<double (*)[kB + 1]>(prep_smem);
+  double (*Bs)[kB + 1] = reinterpret_cast<double (*)[kB + 1]>(prep_smem + sizeof(double) * kB * (kB + 1));
+  const int b = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
   const double* LB = LBall + f * fstride;
   const int64_t bo = ((int64_t)f * nblk + b) * kB * kB;
   const int W = bw + 1;
-  Bs[r][c] = Binv_all[bo + r * kB + c];
-  // L~(32 bi + m, 32 bj + cc), zero outside the matrix and the band
+  // L~(64 bi + m, 64 bj + cc), zero outside the matrix, above the diagonal and outside the band
   auto blk = [&](int bi, int bj, int m, int cc) -> double {
     if (bi < 0 || bi >= nblk || bj < 0) return 0.0;
     const int i = bi * kB + m, col = bj * kB + cc;
-    if (i >= n || i - col > bw) return 0.0;
+    if (i >= n || col > i || i - col > bw) return 0.0;
     return LB[(int64_t)i * W + (col - i + bw)];
   };
+  for (int e = tid; e < kB * kB; e += kPrepThreads) {
+    const int r = e / kB, c = e % kB;
+    O[r][c] = b * kB + r < n ? blk(b, b, r, c) : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (tid < kB) {   // column c of the inverse
+    const int c = tid;
+    for (int r = 0; r < kB; ++r) {
+      double x = r == c ? 1.0 : 0.0;
+      for (int j = c; j < r; ++j) x = fma(-O[r][j], Bs[j][c], x);
+      Bs[r][c] = x;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kB * kB; e += kPrepThreads) B_all[bo + e] = Bs[e / kB][e % kB];
   double* outs[4] = {C1_all, C2_all, D1_all, D2_all};
   for (int which = 0; which < 4; ++which) {
     __syncthreads();
-    if (which == 0) O[r][c] = blk(b, b - 1, r, c);        // L~_{b,b-1}
-    else if (which == 1) O[r][c] = blk(b, b - 2, r, c);   // L~_{b,b-2}
-    else if (which == 2) O[r][c] = blk(b + 1, b, r, c);   // L~_{b+1,b}
-    else O[r][c] = blk(b + 2, b, r, c);                   // L~_{b+2,b}
-    __syncthreads();
-    double acc = 0.0;
-    if (which < 2) {
-#pragma unroll 8
-      for (int m = 0; m < kB; ++m) acc = fma(Bs[r][m], O[m][c], acc);   // B_b O
-    } else {
-#pragma unroll 8
-      for (int m = 0; m < kB; ++m) acc = fma(O[r][m], Bs[m][c], acc);   // O B_b
+    for (int e = tid; e < kB * kB; e += kPrepThreads) {
+      const int r = e / kB, c = e % kB;
+      O[r][c] = which == 0 ? blk(b, b - 1, r, c)
+              : which == 1 ? blk(b, b - 2, r, c)
+              : which == 2 ? blk(b + 1, b, r, c)
+                           : blk(b + 2, b, r, c);
     }
-    outs[which][bo + r * kB + c] = acc;
+    __syncthreads();
+    for (int e = tid; e < kB * kB; e += kPrepThreads) {
+      const int r = e / kB, c = e % kB;
+      double a0 = 0.0, a1 = 0.0;
+      if (which < 2) {
+#pragma unroll 8
+        for (int m = 0; m < kB; m += 2) {
+          a0 = fma(Bs[r][m], O[m][c], a0);
+          a1 = fma(Bs[r][m + 1], O[m + 1][c], a1);
+        }
+      } else {
+#pragma unroll 8
+        for (int m = 0; m < kB; m += 2) {
+          a0 = fma(O[r][m], Bs[m][c], a0);
+          a1 = fma(O[r][m + 1], Bs[m + 1][c], a1);
+        }
+      }
+      outs[which][bo + e] = a0 + a1;
+    }
   }
 }
 
@@ -883,13 +929,18 @@ int cluster_max_active(int CL, int n) {
   return r;
 }
 
-int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
-                    double* C1, double* C2, double* D1, double* D2, cudaStream_t st) {
+int cluster_block_rows() { return kB; }
+
+int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
+               double* D1, double* D2, cudaStream_t st) {
   const int nblk = (m.n_free + kB - 1) / kB;
   const int64_t fstride = (int64_t)m.n_free * (m.bw + 1);
   if (n_fac <= 0) return MQS_OK;
-  k_block_couplings<<<dim3((unsigned)nblk, (unsigned)n_fac), dim3(kB, kB), 0, st>>>(
-      LB, Binv, m.n_free, m.bw, fstride, nblk, C1, C2, D1, D2);
+  const size_t smem = 2 * sizeof(double) * kB * (kB + 1);
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_block_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  k_block_prep<<<dim3((unsigned)nblk, (unsigned)n_fac), kPrepThreads, smem, st>>>(
+      LB, m.n_free, m.bw, fstride, nblk, B, C1, C2, D1, D2);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

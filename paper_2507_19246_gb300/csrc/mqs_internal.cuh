@@ -158,7 +158,8 @@ struct DirectLane {
   const double* LB;        // this lane's band Cholesky factor [n][bw+1]
   const double* invd;      // its reciprocal diagonal [n]
   const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
-  // block couplings of the cluster kernels, [n/32][32][32] each:
+  // 64-row blocks of the cluster kernels, [ceil(n/64)][64][64] each:
+  const double* B64;       // inverse of the unit lower diagonal block
   const double* C1;        // B_b L~_{b,b-1}   [b][r][t]
   const double* C2;        // B_b L~_{b,b-2}   [b][r][t]
   const double* D1;        // L~_{b+1,b} B_b   [b][t][r]
@@ -214,8 +215,9 @@ int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectCons
 
 // mqs_cluster.cu: FP64 stepping with the block solve spread over warps and a
 // lane split over a cluster of `cluster` CTAs (work vector in shared memory)
-int block_couplings(const MeshDev& m, int n_fac, const double* LB, const double* Binv,
-                    double* C1, double* C2, double* D1, double* D2, cudaStream_t st);
+int cluster_block_rows();
+int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
+               double* D1, double* D2, cudaStream_t st);
 int cluster_max_n();
 int cluster_max_active(int CL, int n);
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
