@@ -837,6 +837,124 @@ __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __res
   }
 }
 
+// ---------------------------------------------------------------- band Cholesky on a cluster
+// Right-looking band Cholesky of one factor on a cluster of NC CTAs (the same
+// result and layout as the one-CTA k_band_chol: L in place, L(j, j) on the
+// diagonal, invd = 1 / L(j, j)).  Row i belongs to CTA i mod NC, which scales
+// its entries and applies the rank-1 updates to it in global memory, so no two
+// CTAs write the same row.  Per column j: every CTA scales its rows' entry of
+// column j, writes it back and sends it to every CTA's column buffer; the
+// owner of row j + 1 forms that row's pivot and sends its reciprocal; all
+// sends are asynchronous DSMEM stores counted on the receiver's mbarrier.
+// Then every CTA updates its rows with the received column.
+__device__ __forceinline__ int count_mod(int a, int b, int r, int nc) {   // #{i in [a, b]: i % nc == r}
+  if (b < a) return 0;
+  const int first = a + ((r - a) % nc + nc) % nc;
+  return first > b ? 0 : (b - first) / nc + 1;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LBall,
+                                                       double* __restrict__ invd_all, int n, int bw,
+                                                       int64_t fstride, int32_t* __restrict__ bad) {
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  double* col = reinterpret_cast<double*>(chol_smem);   // [2][bw]: column j of L below the diagonal
+  __shared__ double piv[2];                             // 1 / L(j, j) by column parity
+  __shared__ double l00;
+  __shared__ unsigned long long mb[2];
+  __shared__ int err;
+  const int rho = (int)cluster_rank();
+  const int f = blockIdx.x / NC;
+  double* LB = LBall + f * fstride;
+  double* invd = invd_all + (int64_t)f * n;
+  const int W = bw + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // bytes this CTA receives for column j: the other CTAs' rows and the next pivot
+  auto tx_of = [&](int j) -> uint32_t {
+    if (j >= n) return 0u;
+    const int total = min(bw, n - 1 - j);
+    const int own = count_mod(j + 1, j + total, rho, NC);
+    const int pv = (j + 1 < n && (j + 1) % NC != rho) ? 1 : 0;
+    return (uint32_t)((total - own + pv) * sizeof(double));
+  };
+  if (threadIdx.x == 0) {
+    err = 0;
+    for (int x = 0; x < 2; ++x) {
+      mbar_init(smem_addr(&mb[x]));
+      mbar_arm(smem_addr(&mb[x]), tx_of(x));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    double d = LB[bw];   // every CTA forms the first pivot from A(0, 0)
+    if (!(d > 0.0)) {
+      if (rho == 0) bad[f] = 1;
+      d = 1.0;
+    }
+    l00 = sqrt(d);
+    piv[0] = 1.0 / l00;
+  }
+  cluster_sync_all();   // A(0, 0) read everywhere before CTA 0 overwrites it
+  if (threadIdx.x == 0 && rho == 0) {
+    LB[bw] = l00;
+    invd[0] = piv[0];
+  }
+  for (int j = 0; j < n; ++j) {
+    const int par = j & 1;
+    const int total = min(bw, n - 1 - j);
+    const double inv = piv[par];
+    double* cj = col + par * bw;
+    // own rows of column j: i = first + NC k, i in (j, j + total]
+    const int first = j + 1 + ((rho - (j + 1)) % NC + NC) % NC;
+    const int n_own = first > j + total ? 0 : (j + total - first) / NC + 1;
+    if (threadIdx.x < n_own) {
+      const int i = first + NC * threadIdx.x;
+      const int64_t o = (int64_t)i * W + (j - i + bw);
+      const double l = LB[o] * inv;
+      LB[o] = l;
+      const uint32_t la = smem_addr(cj + (i - j - 1));
+      const uint32_t lm = smem_addr(&mb[par]);
+      for (int p = 0; p < NC; ++p) {
+        if (p == rho)
+          cj[i - j - 1] = l;
+        else
+          st_async(map_rank(la, p), l, map_rank(lm, p));
+      }
+      if (i == j + 1) {   // this CTA owns row j + 1: its pivot
+        const int64_t od = (int64_t)(j + 1) * W + bw;
+        double d = fma(-l, l, LB[od]);   // the rank-1 update of the diagonal, as in k_band_chol
+        if (!(d > 0.0)) {
+          bad[f] = 1;
+          d = 1.0;
+        }
+        const double L = sqrt(d);
+        const double r = 1.0 / L;
+        LB[od] = L;
+        invd[j + 1] = r;
+        const uint32_t pa = smem_addr(&piv[par ^ 1]);
+        for (int p = 0; p < NC; ++p) {
+          if (p == rho)
+            piv[par ^ 1] = r;
+          else
+            st_async(map_rank(pa, p), r, map_rank(lm, p));
+        }
+      }
+    }
+    mbar_wait(smem_addr(&mb[par]), (uint32_t)((j >> 1) & 1), &err);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arm(smem_addr(&mb[par]), tx_of(j + 2));   // column j + 2
+    // rank-1 update of the own rows (j + 1, j + total], entries j + 1 .. i
+    for (int k = warp; k < n_own; k += kNW) {
+      const int i = first + NC * k;
+      if (i == j + 1) continue;
+      const double li = cj[i - j - 1];
+      double* row = LB + (int64_t)i * W + bw - i;       // row[c] = A(i, c)
+      for (int c = j + 1 + lane; c <= i; c += 32) row[c] = fma(-li, cj[c - j - 1], row[c]);
+    }
+    __syncthreads();
+  }
+  cluster_sync_all();
+  if (threadIdx.x == 0 && err) bad[f] = 1;
+}
+
 // ---------------------------------------------------------------- launch helpers
 template <int CL>
 const void* propagate_fn() { return reinterpret_cast<const void*>(&k_cluster_propagate<CL>); }
@@ -930,6 +1048,34 @@ int cluster_max_active(int CL, int n) {
 }
 
 int cluster_block_rows() { return kB; }
+
+// Band Cholesky of n_fac factors, one cluster of 8 CTAs each (see
+// k_band_chol_cl); MQS_ENOTSUP-style refusal is left to the caller, which
+// uses the one-CTA kernel when the factors fill the GPU.
+int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, int n_fac,
+                      int32_t* bad, cudaStream_t st) {
+  constexpr int NC = 8;
+  if (n_fac <= 0) return MQS_OK;
+  const size_t smem = 2 * sizeof(double) * (size_t)std::max(bw, 1);
+  MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol_cl<NC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_fac * NC));
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  MQS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_chol_cl<NC>, LB, invd, n, bw, fstride, bad));
+  count_launch();
+  return MQS_OK;
+}
+int band_chol_cluster_size() { return 8; }
 
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
                double* D1, double* D2, cudaStream_t st) {

@@ -26,6 +26,8 @@
 #include "mqs_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
+#include <type_traits>
 
 namespace mqs {
 namespace {
@@ -634,12 +636,24 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, T* LB,
                                                             vs, n_fac, fstride, LB);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
-  const size_t smem = (size_t)std::max(bw, 1) * sizeof(T);
-  MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  k_band_chol<T><<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
-  MQS_CUDA_TRY(cudaGetLastError());
-  count_launch();
+  int n_sm = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // few factors: each on a cluster of CTAs (env MQS_CHOL_CLUSTER=0/1 forces the choice)
+  const char* ev = getenv("MQS_CHOL_CLUSTER");
+  const bool few = n_fac * band_chol_cluster_size() <= n_sm;
+  const bool use_cluster = ev && *ev ? atoi(ev) != 0 : few;
+  if (std::is_same<T, double>::value && use_cluster) {
+    MQS_TRY(band_chol_cluster(reinterpret_cast<double*>(LB), reinterpret_cast<double*>(invd),
+                              m.n_free, bw, fstride, n_fac, bad, st));
+  } else {
+    const size_t smem = (size_t)std::max(bw, 1) * sizeof(T);
+    MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    k_band_chol<T><<<n_fac, kDT, smem, st>>>(LB, invd, m.n_free, bw, fstride, bad);
+    MQS_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
   k_band_unit<T><<<grid_of((int64_t)m.n_free * n_fac, 8), dim3(32, 8), 0, st>>>(LB, invd, m.n_free,
                                                                              bw, fstride, n_fac);
   MQS_CUDA_TRY(cudaGetLastError());

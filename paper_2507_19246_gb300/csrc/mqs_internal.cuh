@@ -216,6 +216,9 @@ int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectCons
 // mqs_cluster.cu: FP64 stepping with the block solve spread over warps and a
 // lane split over a cluster of `cluster` CTAs (work vector in shared memory)
 int cluster_block_rows();
+int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, int n_fac,
+                      int32_t* bad, cudaStream_t st);
+int band_chol_cluster_size();
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
                double* D1, double* D2, cudaStream_t st);
 int cluster_max_n();

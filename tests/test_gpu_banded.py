@@ -279,3 +279,26 @@ def test_cluster_split_lane_is_independent_of_batch(ctx, mqs, monkeypatch, clust
         out.append((ctx.read_qoi(b)[0], ctx.read_state(b, 0)))
     assert out[0][0][4, 0] == out[1][0][0, 0]
     assert np.array_equal(out[0][1][4], out[1][1][0])
+
+
+@pytest.mark.parametrize("n_samples", [1, 3])
+def test_cluster_band_cholesky_matches_one_cta_bitwise(ctx, mqs, monkeypatch, n_samples):
+    """The band Cholesky on a cluster of CTAs (per-column DSMEM exchange)
+    performs the same operations per entry as the one-CTA kernel: the states
+    after stepping with either factor are bitwise equal, and match the oracle."""
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(n_samples, 0, seed=21)
+    mid = ctx.upload_mesh(mesh)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("MQS_CHOL_CLUSTER", flag)
+        b = ctx.set_samples(mid, p)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, configs.PERIOD / 8, 50.0, mqs.MQS_QOI_JOULE)
+        ctx.propagate(b, 0, configs.level_dt(0))
+        q, st = ctx.read_qoi(b)
+        assert not st.any()
+        out.append((q.copy(), ctx.read_state(b, 0)))
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
+    qo, ao, _ = stepper.solve_sample(mesh, p[0], configs.level_dt(0), 8, stepper.QOI_JOULE)
+    assert abs(out[0][0][0, 0] - qo) <= TOL * abs(qo) and _rel(out[0][1][0], ao) <= TOL
