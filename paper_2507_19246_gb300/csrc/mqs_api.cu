@@ -638,17 +638,19 @@ int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
 // Cluster size of the FP64 stepping kernels with the work vector in shared
 // memory; 0 selects the one-CTA kernels of mqs_direct.cu (mixed precision,
 // work vector in L2).  The widest split (8, 4, 2 CTAs per lane) whose clusters
-// all fit the SMs in one wave, else 1.  Measured on the 20k-node annulus: one
-// lane (the coarse sweep) steps fastest on 8 CTAs; 64 lanes (the fine batch)
-// on 2 CTAs each, 2.3x faster than on one.  env MQS_DIRECT_CLUSTER=0/1/2/4/8
-// forces a choice.
+// all fit the SMs in one wave; with more lanes, 2 CTAs per lane in several
+// waves.  Measured on the 20k-node annulus: one lane (the coarse sweep) steps
+// fastest on 8 CTAs; 64 lanes on 2 CTAs each (2.55 ms per step); the
+// one-CTA form of these kernels (8 ms per step) and the one-CTA kernel of
+// mqs_direct.cu (7 ms) lose to 2 CTAs per lane even at two waves.
+// env MQS_DIRECT_CLUSTER=0/1/2/4/8 forces a choice.
 int direct_cluster(const MeshDev& m, int lanes, int n_sm, const DirectConst& kc) {
   if (kc.mixed || !kc.w_in_smem || m.n_free > cluster_max_n()) return 0;
   const int forced = env_int("MQS_DIRECT_CLUSTER", -1);
   if (forced == 0 || forced == 1 || forced == 2 || forced == 4 || forced == 8) return forced;
   for (int cl : {8, 4, 2})
     if (lanes * cl <= n_sm && lanes <= cluster_max_active(cl, m.n_free)) return cl;
-  return 1;
+  return cluster_max_active(2, m.n_free) > 0 ? 2 : 0;
 }
 
 // lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
