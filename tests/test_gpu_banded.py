@@ -302,3 +302,54 @@ def test_cluster_band_cholesky_matches_one_cta_bitwise(ctx, mqs, monkeypatch, n_
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
     qo, ao, _ = stepper.solve_sample(mesh, p[0], configs.level_dt(0), 8, stepper.QOI_JOULE)
     assert abs(out[0][0][0, 0] - qo) <= TOL * abs(qo) and _rel(out[0][1][0], ao) <= TOL
+
+
+@pytest.mark.parametrize("cluster", ["1", "2", "4", "8"])
+def test_cluster_split_ragged_blocks(ctx, mqs, monkeypatch, cluster):
+    """n = 225 unknowns: three full 64-row blocks and a ragged fourth, every
+    cluster size, energy QoI, plain stepping and Parareal against the oracle."""
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", cluster)
+    mesh = meshes.unit_square(16)
+    p = params.square_samples(2)
+    dt = configs.PERIOD / 40
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 24 * dt, 50.0, mqs.MQS_QOI_ENERGY)
+    ctx.propagate(b, 0, dt)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    for s in range(2):
+        qo, ao, _ = stepper.solve_sample(mesh, p[s], dt, 24, stepper.QOI_ENERGY)
+        assert abs(q[s, 0] - qo) <= TOL * abs(qo) and _rel(a[s], ao) <= TOL, s
+    b = ctx.set_samples(mid, p[:1])
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 24 * dt, 50.0, mqs.MQS_QOI_ENERGY)
+    K = ctx.propagate(b, 0, dt, n_slices=6, coarse_factor=2, max_par_iters=6, par_tol=1e-9)
+    q, st = ctx.read_qoi(b)
+    assert not st.any()
+    ref = parareal.parareal_sample(fem.Discretisation(mesh, p[0]), dt, 24, 6, 2, 1e-9,
+                                   stepper.QOI_ENERGY)
+    assert K == ref["iters"]
+    q_ref = stepper.qoi_finish(stepper.QOI_ENERGY, ref["qoi_raw"], 24, dt)
+    assert abs(q[0, 0] - q_ref) <= TOL * abs(q_ref)
+
+
+def test_cluster_band_cholesky_tiny(ctx, mqs, monkeypatch):
+    """9 unknowns on a cluster of 8 CTAs: most CTAs own one row or none."""
+    monkeypatch.setenv("MQS_CHOL_CLUSTER", "1")
+    mesh = meshes.unit_square(4)
+    p = params.square_samples(1)
+    dt = configs.PERIOD / 20
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 5 * dt, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 0, dt)
+    q, st = ctx.read_qoi(b)
+    a = ctx.read_state(b, 0)
+    assert not st.any()
+    qo, ao, _ = stepper.solve_sample(mesh, p[0], dt, 5, stepper.QOI_JOULE)
+    assert abs(q[0, 0] - qo) <= TOL * abs(qo) and _rel(a[0], ao) <= TOL
