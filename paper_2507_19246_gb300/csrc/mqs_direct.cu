@@ -14,7 +14,10 @@
 //  * k_band_fill   scatters the lower-band entries of each sample's A values.
 //  * k_band_chol   right-looking band Cholesky, one CTA per factor, in place:
 //                  for each column j, L_jj = sqrt(A_jj), scale the column,
-//                  rank-1 update of the bw x bw trailing triangle.
+//                  rank-1 update of the bw x bw trailing triangle.  Used when
+//                  the factors fill the GPU; a few factors go to the cluster
+//                  kernel k_band_chol_cl (mqs_cluster.cu), which gives the
+//                  same factor bit for bit.
 //  * k_direct_propagate  one CTA per lane walks all time steps: right-hand
 //                  side (original order) scattered into the permuted work
 //                  vector, blocked forward and backward substitution (32-row
@@ -23,6 +26,10 @@
 //                  gather back, QoI and y = M a.
 //  * k_direct_chain  the Parareal coarse sweep (one CTA per sample) with the
 //                  Eq. 12 correction and jump norms fused, lane-major state.
+// The two stepping kernels serve the mixed-precision form and FP64 batches
+// too large for a shared-memory work vector per lane (256 threads, work
+// vector in L2); FP64 stepping with the work vector in shared memory runs
+// on the cluster kernels of mqs_cluster.cu.
 #include "mqs_internal.cuh"
 
 #include <algorithm>
