@@ -840,13 +840,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __res
 // ---------------------------------------------------------------- band Cholesky on a cluster
 // Right-looking band Cholesky of one factor on a cluster of NC CTAs (the same
 // result and layout as the one-CTA k_band_chol: L in place, L(j, j) on the
-// diagonal, invd = 1 / L(j, j)).  Row i belongs to CTA i mod NC, which scales
-// its entries and applies the rank-1 updates to it in global memory, so no two
-// CTAs write the same row.  Per column j: every CTA scales its rows' entry of
-// column j, writes it back and sends it to every CTA's column buffer; the
-// owner of row j + 1 forms that row's pivot and sends its reciprocal; all
-// sends are asynchronous DSMEM stores counted on the receiver's mbarrier.
-// Then every CTA updates its rows with the received column.
+// diagonal, invd = 1 / L(j, j)).  Row i belongs to CTA i mod NC, which keeps
+// it in a shared-memory ring from the column where it enters the band window
+// until it is final, then writes it back once.  Per column j: every CTA
+// scales its rows' entry of column j and sends it to every CTA's column
+// buffer; the owner of row j + 1 forms that row's pivot and sends its
+// reciprocal; all sends are asynchronous DSMEM stores counted on the
+// receiver's mbarrier.  Then every CTA applies the rank-1 update to its rows.
 __device__ __forceinline__ int count_mod(int a, int b, int r, int nc) {   // #{i in [a, b]: i % nc == r}
   if (b < a) return 0;
   const int first = a + ((r - a) % nc + nc) % nc;
@@ -854,12 +854,23 @@ __device__ __forceinline__ int count_mod(int a, int b, int r, int nc) {   // #{i
 }
 
 template <int NC>
+struct CholRing {
+  static int slots(int bw) { return (bw + 1 + NC - 1) / NC + 2; }
+  static size_t bytes(int bw) {
+    return sizeof(double) * ((size_t)slots(bw) * (bw + 1) + 2 * (size_t)std::max(bw, 1));
+  }
+};
+
+template <int NC>
 __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LBall,
                                                        double* __restrict__ invd_all, int n, int bw,
                                                        int64_t fstride, int32_t* __restrict__ bad) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
-  double* col = reinterpret_cast<double*>(chol_smem);   // [2][bw]: column j of L below the diagonal
-  __shared__ double piv[2];                             // 1 / L(j, j) by column parity
+  const int W = bw + 1;
+  const int RING = (bw + 1 + NC - 1) / NC + 2;
+  double* ring = reinterpret_cast<double*>(chol_smem);   // [RING][W]: own rows of the window
+  double* col = ring + (size_t)RING * W;                  // [2][bw]: column j of L below the diagonal
+  __shared__ double piv[2];                               // 1 / L(j, j) by column parity
   __shared__ double l00;
   __shared__ unsigned long long mb[2];
   __shared__ int err;
@@ -867,8 +878,18 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
   const int f = blockIdx.x / NC;
   double* LB = LBall + f * fstride;
   double* invd = invd_all + (int64_t)f * n;
-  const int W = bw + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto row_of = [&](int i) -> double* { return ring + (size_t)((i / NC) % RING) * W; };
+  auto load_row = [&](int i) {          // all threads of the CTA
+    const double* src = LB + (int64_t)i * W;
+    double* dst = row_of(i);
+    for (int d = threadIdx.x; d < W; d += kNT) dst[d] = src[d];
+  };
+  auto store_row = [&](int i) {
+    const double* src = row_of(i);
+    double* dst = LB + (int64_t)i * W;
+    for (int d = threadIdx.x; d < W; d += kNT) dst[d] = src[d];
+  };
   // bytes this CTA receives for column j: the other CTAs' rows and the next pivot
   auto tx_of = [&](int j) -> uint32_t {
     if (j >= n) return 0u;
@@ -877,6 +898,7 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
     const int pv = (j + 1 < n && (j + 1) % NC != rho) ? 1 : 0;
     return (uint32_t)((total - own + pv) * sizeof(double));
   };
+  for (int i = rho; i < min(n, bw + 1); i += NC) load_row(i);   // rows in the window of column 0
   if (threadIdx.x == 0) {
     err = 0;
     for (int x = 0; x < 2; ++x) {
@@ -892,10 +914,14 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
     l00 = sqrt(d);
     piv[0] = 1.0 / l00;
   }
-  cluster_sync_all();   // A(0, 0) read everywhere before CTA 0 overwrites it
-  if (threadIdx.x == 0 && rho == 0) {
-    LB[bw] = l00;
-    invd[0] = piv[0];
+  cluster_sync_all();   // A(0, 0) read everywhere before CTA 0 writes row 0 back
+  if (rho == 0) {
+    if (threadIdx.x == 0) {
+      row_of(0)[bw] = l00;
+      invd[0] = piv[0];
+    }
+    __syncthreads();
+    store_row(0);
   }
   for (int j = 0; j < n; ++j) {
     const int par = j & 1;
@@ -907,9 +933,9 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
     const int n_own = first > j + total ? 0 : (j + total - first) / NC + 1;
     if (threadIdx.x < n_own) {
       const int i = first + NC * threadIdx.x;
-      const int64_t o = (int64_t)i * W + (j - i + bw);
-      const double l = LB[o] * inv;
-      LB[o] = l;
+      double* row = row_of(i);
+      const double l = row[j - i + bw] * inv;
+      row[j - i + bw] = l;
       const uint32_t la = smem_addr(cj + (i - j - 1));
       const uint32_t lm = smem_addr(&mb[par]);
       for (int p = 0; p < NC; ++p) {
@@ -919,15 +945,14 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
           st_async(map_rank(la, p), l, map_rank(lm, p));
       }
       if (i == j + 1) {   // this CTA owns row j + 1: its pivot
-        const int64_t od = (int64_t)(j + 1) * W + bw;
-        double d = fma(-l, l, LB[od]);   // the rank-1 update of the diagonal, as in k_band_chol
+        double d = fma(-l, l, row[bw]);   // the rank-1 update of the diagonal, as in k_band_chol
         if (!(d > 0.0)) {
           bad[f] = 1;
           d = 1.0;
         }
         const double L = sqrt(d);
         const double r = 1.0 / L;
-        LB[od] = L;
+        row[bw] = L;
         invd[j + 1] = r;
         const uint32_t pa = smem_addr(&piv[par ^ 1]);
         for (int p = 0; p < NC; ++p) {
@@ -946,9 +971,12 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
       const int i = first + NC * k;
       if (i == j + 1) continue;
       const double li = cj[i - j - 1];
-      double* row = LB + (int64_t)i * W + bw - i;       // row[c] = A(i, c)
+      double* row = row_of(i) + bw - i;                 // row[c] = A(i, c)
       for (int c = j + 1 + lane; c <= i; c += 32) row[c] = fma(-li, cj[c - j - 1], row[c]);
     }
+    // row j + 1 is final: write it back; row j + 1 + bw enters the window at column j + 1
+    if (j + 1 < n && (j + 1) % NC == rho) store_row(j + 1);
+    if (j + 1 + bw < n && (j + 1 + bw) % NC == rho) load_row(j + 1 + bw);
     __syncthreads();
   }
   cluster_sync_all();
@@ -1056,7 +1084,7 @@ int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, 
                       int32_t* bad, cudaStream_t st) {
   constexpr int NC = 8;
   if (n_fac <= 0) return MQS_OK;
-  const size_t smem = 2 * sizeof(double) * (size_t)std::max(bw, 1);
+  const size_t smem = CholRing<NC>::bytes(bw);
   MQS_CUDA_TRY(cudaFuncSetAttribute(k_band_chol_cl<NC>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
@@ -1076,6 +1104,9 @@ int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, 
   return MQS_OK;
 }
 int band_chol_cluster_size() { return 8; }
+// The cluster kernel keeps the window's rows in shared memory: bandwidths up
+// to ~440 on 8 CTAs.
+bool band_chol_cluster_fits(int bw) { return CholRing<8>::bytes(bw) <= 200 * 1024; }
 
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
                double* D1, double* D2, cudaStream_t st) {

@@ -650,7 +650,7 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, T* LB,
   const char* ev = getenv("MQS_CHOL_CLUSTER");
   const bool few = n_fac * band_chol_cluster_size() <= n_sm;
   const bool use_cluster = ev && *ev ? atoi(ev) != 0 : few;
-  if (std::is_same<T, double>::value && use_cluster) {
+  if (std::is_same<T, double>::value && use_cluster && band_chol_cluster_fits(bw)) {
     MQS_TRY(band_chol_cluster(reinterpret_cast<double*>(LB), reinterpret_cast<double*>(invd),
                               m.n_free, bw, fstride, n_fac, bad, st));
   } else {

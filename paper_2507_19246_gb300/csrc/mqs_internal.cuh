@@ -219,6 +219,7 @@ int cluster_block_rows();
 int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, int n_fac,
                       int32_t* bad, cudaStream_t st);
 int band_chol_cluster_size();
+bool band_chol_cluster_fits(int bw);
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
                double* D1, double* D2, cudaStream_t st);
 int cluster_max_n();
