@@ -562,7 +562,7 @@ struct Subst {
 };
 
 // ---------------------------------------------------------------- stepping
-// Own nodes of rank q: band rows pi with (pi mod 32) in [q*R, q*R + R).
+// Own nodes of rank q: band rows pi with (pi mod 64) in [q*R, q*R + R), R = 64/CL.
 template <int CL>
 struct Own {
   int n, q;

@@ -353,3 +353,32 @@ def test_cluster_band_cholesky_tiny(ctx, mqs, monkeypatch):
     assert not st.any()
     qo, ao, _ = stepper.solve_sample(mesh, p[0], dt, 5, stepper.QOI_JOULE)
     assert abs(q[0, 0] - qo) <= TOL * abs(qo) and _rel(a[0], ao) <= TOL
+
+
+def test_banded_parareal_level_pair(ctx, mqs):
+    """MLMC level with Parareal on the fine level and the companion level l-1
+    solved sequentially (its factor on the main stream, the fine factor on the
+    side stream): both QoIs against the oracle."""
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(2, 1, seed=31)
+    dt1, dt0 = configs.level_dt(1), configs.level_dt(0)
+    n_steps, M, cf, tol = 64, 8, 2, 1e-9
+    mid = ctx.upload_mesh(mesh)
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, n_steps * dt1, 50.0, mqs.MQS_QOI_JOULE)
+    K = ctx.propagate(b, 1, dt1, dt_prev=dt0, n_slices=M, coarse_factor=cf, max_par_iters=M,
+                      par_tol=tol)
+    q, st = ctx.read_qoi(b)
+    assert not st.any()
+    Ks = []
+    for s in range(2):
+        d = fem.Discretisation(mesh, p[s])
+        ref = parareal.parareal_sample(d, dt1, n_steps, M, cf, tol, stepper.QOI_JOULE)
+        Ks.append(ref["iters"])
+        qc, _, _ = stepper.solve_sample(mesh, p[s], dt0, n_steps // 2, stepper.QOI_JOULE)
+        assert abs(q[s, 1] - qc) <= TOL * abs(qc), s
+        if ref["iters"] == K:
+            q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt1)
+            assert abs(q[s, 0] - q_ref) <= TOL * abs(q_ref), s
+    assert K == max(Ks)
