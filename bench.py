@@ -14,7 +14,8 @@ and the MLMC moment update, read back to device memory.  Throughput counts
 serial-equivalent fine steps: 4096 x 19584 sample-DoF-steps per solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--precision fp64|mixed] [--workload parareal20k|mcsquare]
+                    [--precision fp64|mixed] [--solver banded|pcg]
+                    [--workload parareal20k|parareal20k_short|mlmc20k|mlmc20k_short|mcsquare]
 
 With N > 1 (torchrun) every rank runs an independent replica ("replicas
 only": the Parareal solve of one sample has no cross-GPU exchange); value is
@@ -200,8 +201,10 @@ def oracle_sample(wl, n_steps):
     """Time the oracle's serial fine propagator on `n_steps` steps of the
     workload's first sample in a single-threaded subprocess."""
     mesh_fn = {"parareal_annulus20k": "annulus('20k')", "parareal_annulus20k_short": "annulus('20k')",
+               "mlmc_annulus20k": "annulus('20k')", "mlmc_annulus20k_short": "annulus('20k')",
                "mc_square16": "unit_square(16)"}[wl["name"]]
     params_expr = ("params.annulus_nominal(1)" if wl["name"].startswith("parareal")
+                   else "params.annulus_samples(1, 0)" if wl["name"].startswith("mlmc")
                    else "params.square_samples(1)")
     code = ORACLE_SNIPPET.format(root=ROOT, mesh_fn=mesh_fn, params_expr=params_expr,
                                  n_steps=n_steps, dt=wl["dt"], qoi=wl["qoi"])
@@ -212,23 +215,55 @@ def oracle_sample(wl, n_steps):
     return r["units"] / r["seconds"], r["seconds"]
 
 
+def static_config(wl, args, n_free, nnz):
+    """The workload part of the JSON line's config, shared by both arms."""
+    if "mlmc" in wl:
+        c = wl["mlmc"]
+        return {"workload": wl["name"], "n_free": n_free, "levels": len(c.n_per_level),
+                "n_per_level": list(c.n_per_level), "periods": c.periods,
+                "solver": args.solver, "precision": args.precision,
+                "solve_steps": c.solve_steps()}
+    return {"workload": wl["name"], "mesh": wl["mesh"].name, "n_free": n_free, "nnz": nnz,
+            "samples": int(wl["params"].shape[0]), "steps": wl["n_steps"], "dt": wl["dt"],
+            "slices": wl["n_slices"], "coarse_factor": wl["cf"], "parareal_tol": wl["par_tol"],
+            "precision": args.precision, "solver": args.solver}
+
+
+def mesh_pattern(mesh):
+    """Free unknowns and nonzeros of the P1 pattern over them (topology only)."""
+    free = [v for v in range(len(mesh.xy)) if not mesh.dirichlet[v]]
+    fid = {v: k for k, v in enumerate(free)}
+    pairs = set()
+    for t in mesh.tri:
+        ids = [fid.get(int(v)) for v in t]
+        for a in ids:
+            for b in ids:
+                if a is not None and b is not None:
+                    pairs.add((a, b))
+    return len(free), len(pairs)
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
-    n_steps = 256 if wl["name"].startswith("parareal") else wl["n_steps"]
+    # a bounded sample of serial fine steps: the Parareal sample's fine step,
+    # the MLMC workload's level-0 step, or the whole small MC run
+    n_steps = 256 if wl["name"].startswith(("parareal", "mlmc")) else wl["n_steps"]
+    total = wl["n_steps"] if wl["n_steps"] else wl["mlmc"].solve_steps()
     vals = []
     for i in range(args.warmup + args.steps):
         v, _ = oracle_sample(wl, n_steps)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
-    sample = (f"serial fine implicit-Euler propagator of the oracle, {n_steps} of "
-              f"{wl['n_steps']} steps of the workload's sample per bench step, 1 thread")
+    sample = (f"serial fine implicit-Euler propagator of the oracle, {n_steps} of the "
+              f"workload's {total} sample-steps (first sample, level-0 step size for MLMC) "
+              f"per bench step, 1 thread")
     line = {"impl": "reference", "metric": "sample-DoF-steps/s", "value": value,
             "unit": "sample-DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"]},
+            "config": static_config(wl, args, *mesh_pattern(wl["mesh"])),
             "e2e": {"value": value, "unit": "sample-DoF-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": value, "unit": "sample-DoF-steps/s", "cores": 1,
@@ -387,14 +422,10 @@ def run_ours(args, wl, rank, world, dist):
         "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": wl["name"], "mesh": wl["mesh"].name, "n_free": n_free, "nnz": nnz,
-                   "samples": ns, "steps": wl["n_steps"], "dt": wl["dt"],
-                   "slices": wl["n_slices"], "coarse_factor": wl["cf"],
-                   "parareal_tol": wl["par_tol"], "linear_tol": tol_lin,
-                   "precision": args.precision, "solver": args.solver,
-                   "parareal_iters": ks[-1],
-                   "l2": "flushed (512 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(static_config(wl, args, n_free, nnz), linear_tol=tol_lin,
+                       parareal_iters=ks[-1],
+                       l2="flushed (512 MB write) before every timed step",
+                       parallelism=f"replicas x{world}"),
         "p50_ms": statistics.median(times), "p99_ms": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
         "time_to_solution_s": ms_total / args.steps / 1e3,
         "cg_iters_per_lane_step": (st[0] / max(st[1], 1)),
@@ -470,10 +501,7 @@ def run_mlmc(args, wl):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "n_free": n_free, "levels": L,
-                       "n_per_level": list(c.n_per_level), "periods": c.periods,
-                       "solver": args.solver, "precision": args.precision,
-                       "solve_steps": c.solve_steps()},
+            "config": static_config(wl, args, n_free, None),
             "time_to_rmse_s": statistics.median(times), "estimate": est, "rmse": rmse,
             "levels": lv.tolist(), "clocks": clk.summary(),
             "kernel_ms": {"stepping": prof[2] / len(times), "coarse_sweep": prof[4] / len(times)}}
