@@ -679,6 +679,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, 
   kc.tol2 = tol * tol;
   kc.max_sweeps = max_sweeps;
   kc.cluster = direct_cluster(m, lanes, n_sm, kc);
+  kc.stall_test = env_int("MQS_TEST_STALL", 0) == 1 ? 1 : 0;
   return kc;
 }
 

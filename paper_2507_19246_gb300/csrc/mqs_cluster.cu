@@ -6,12 +6,12 @@
 // FP64 on this GPU retires one warp instruction per 64 cycles on each of the
 // four SM sub-partitions, whatever the number of active lanes, and a dependent
 // FP64 instruction waits as long.  The substitution is therefore organised so
-// that (1) the dense work of every 32-row block runs on four warps (one per
-// sub-partition) instead of one, (2) the band products (GEMV) run on other
+// that (1) the dense work of every 64-row block runs on several warps
+// instead of one, (2) the band products (GEMV) run on other
 // warps with long per-lane FMA chains and few reduction levels, and (3) one
 // lane may be split over a cluster of CL CTAs on CL SMs.
 //
-// Algebra (unit lower factor L~ = D^-1 L, 32-row blocks, B_b = L~_bb^-1):
+// Algebra (unit lower factor L~ = D^-1 L, 64-row blocks, B_b = L~_bb^-1):
 //   forward  L~ y = w:    y_b = B_b (w_b - P_b) - C1_b y_{b-1} - C2_b y_{b-2},
 //                         C1_b = B_b L~_{b,b-1}, C2_b = B_b L~_{b,b-2},
 //                         P_b = sum_{k <= b-3} L~_bk y_k
@@ -27,7 +27,7 @@
 // counters in shared memory, never through a CTA-wide barrier.
 //
 // Cluster split: every CTA keeps a full copy of the permuted work vector in
-// shared memory and owns rows q*R .. q*R+R-1 (R = 32/CL) of every block, in
+// shared memory and owns rows q*R .. q*R+R-1 (R = 64/CL) of every block, in
 // the band ordering.  Per block it computes s for its own rows and its share
 // of the block solve, v_q = pre_q - C1_b[:, own] y_{b-1}[own], which it sends
 // to every CTA of the cluster with asynchronous DSMEM stores that complete on
@@ -260,6 +260,7 @@ struct Subst {
   int x_r, x_g;          // exchange lane: block row, term group (own rows t = x_g + LPR k)
   int p_r, p_g;          // pre lane: block row, term group (own rows t = p_g + LPRP k)
   int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
+  bool stall = false;    // test hook (one-CTA form): the first wait is on a count nothing reaches
 
   __device__ Subst(const DirectLane& D, double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
       : LB(D.LB), B(D.B64), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), w(w_), sm(sm_), n(n_),
@@ -463,6 +464,13 @@ struct Subst {
             const int row = j * kB + q * S::R + t;
             sm.s[j & 3][t] = row < n ? w[row] : 0.0;
           }
+      if constexpr (CL == 1) {
+        // test hook: a wait that runs out of polls sets the error flag; every
+        // later wait then returns at once and the lane reports MQS_ST_TIMEOUT.
+        // The one-CTA form has no cross-CTA traffic, so nothing is left in
+        // flight when the CTA ends.
+        if (stall && rounds == 0) wait_count(&sm.sdone, 1 << 30, &sm.err);
+      }
       GemvDesc cur = gemv_desc(2);
       gemv_load(cur, pf);
       group_sync(2, S::GW * 32);
@@ -709,6 +717,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
   const DirectLane D = lanes[blockIdx.x / CL];
   cluster_setup<CL>(sm);
   Subst<CL> sub(D, w, sm, kc.n, kc.bw, (int)q);
+  sub.stall = kc.stall_test != 0;
   const double part = cluster_integrate<CL>(kc, D, D.init_from_a0 ? D.a0 : nullptr, D.n_steps,
                                             D.k0, q, sub, w, true);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
@@ -733,6 +742,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   const int sample = D.sample;
   cluster_setup<CL>(sm);
   Subst<CL> sub(D, w, sm, n, kc.bw, (int)q);
+  sub.stall = kc.stall_test != 0;
   for (int s = ch.s_begin; s < ch.M - 1; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
     cluster_integrate<CL>(kc, D, ch.U + base, ch.steps_per_slice,

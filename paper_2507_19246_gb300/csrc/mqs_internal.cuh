@@ -195,6 +195,9 @@ struct DirectConst {
   double tol2;             // mixed: stop when ||b - A x||^2 <= tol2 ||b||^2
   int32_t max_sweeps;      // mixed: refinement sweep limit per step
   int32_t cluster;         // 0: one-CTA kernels of mqs_direct.cu; 1, 2, 4, 8: CTAs per lane
+  int32_t stall_test;      // 1: the one-CTA cluster kernel's first wait is on a count
+                           //    nothing reaches (tests the bounded wait and its status)
+  int32_t pad3_;
 };
 
 struct DirectChain {

@@ -382,3 +382,31 @@ def test_banded_parareal_level_pair(ctx, mqs):
             q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt1)
             assert abs(q[s, 0] - q_ref) <= TOL * abs(q_ref), s
     assert K == max(Ks)
+
+
+def test_expired_wait_reports_timeout_and_context_stays_usable(ctx, mqs, monkeypatch):
+    """A wait on a count nothing reaches (test hook, one-CTA form: no cross-CTA
+    traffic) runs out of polls: the lane reports MQS_ST_TIMEOUT, and the same
+    context then solves correctly."""
+    mesh = meshes.unit_square(8)
+    p = params.square_samples(2)
+    dt = configs.PERIOD / 20
+    mid = ctx.upload_mesh(mesh)
+    monkeypatch.setenv("MQS_DIRECT_WIDE", "1")
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", "1")
+    monkeypatch.setenv("MQS_TEST_STALL", "1")
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 4 * dt, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 0, dt)
+    _, st = ctx.read_qoi(b)
+    assert (st & mqs.MQS_ST_TIMEOUT).all()
+    monkeypatch.delenv("MQS_TEST_STALL")
+    b = ctx.set_samples(mid, p)
+    ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+    ctx.set_time(b, 0.0, 4 * dt, 50.0, mqs.MQS_QOI_JOULE)
+    ctx.propagate(b, 0, dt)
+    q, st = ctx.read_qoi(b)
+    assert not st.any()
+    qo, _, _ = stepper.solve_sample(mesh, p[0], dt, 4, stepper.QOI_JOULE)
+    assert abs(q[0, 0] - qo) <= TOL * abs(qo)
