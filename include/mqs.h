@@ -211,16 +211,18 @@ int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rms
  *
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory while they run -- a host application driving
- * the GPU from a real-time or signal-safe path, a runtime that partitions all
- * device memory into its own pools at start-up, or code that forbids
- * allocation inside a region it records.  They own every input and output;
- * the library works in a static device scratch array of 32 MiB that each GPU
- * loading the library holds until the process exits.
+ * the GPU from a real-time or signal-safe path, where cudaMalloc may block or
+ * take locks, or a runtime that partitions all device memory into its own
+ * pools at start-up, so that a cudaMalloc would fail or compete with them.
+ * They own every input and output; the library works in a static device
+ * scratch array of 32 MiB that each GPU loading the library holds until the
+ * process exits.
  *
  * It runs the same stepping kernel as mqs_propagate on n_lanes independent
  * lanes from a(t0) = 0 (Eq. 7 with the same Jacobi-PCG and the same QoI
  * definitions), with matrices the caller has assembled:
- *   device          CUDA device ordinal (made current)
+ *   device          CUDA device ordinal (current during the call; the caller's
+ *                   current device is restored before the call returns)
  *   cuda_stream     cudaStream_t or NULL; all work is enqueued on it
  *   n, rowptr, colidx, nnz   device, CSR pattern of the n x n free-unknown matrices
  *                   (int32, columns ascending within a row, at most 32 per row)
@@ -250,6 +252,15 @@ int mqs_propagate_noalloc(int32_t device, void* cuda_stream, int32_t n, const in
                           const double* src_phase, double t0, double dt, int32_t n_steps,
                           double freq_hz, int32_t qoi_kind, double cg_tol, int32_t cg_max_iters,
                           double* a_out, double* qoi_out, int32_t* status_out);
+
+/* Test hook, for tests of the failure path only (0 = off, the default).
+ * MQS_TEST_HOOK_STALL: on this context, the first wait of every banded
+ * stepping lane that runs as one CTA per lane (cluster kernels with one CTA)
+ * waits on a count that nothing reaches, so that the bounded wait runs out
+ * and the lane reports MQS_ST_TIMEOUT with an invalid result.  Other contexts
+ * and other launch shapes are not affected. */
+#define MQS_TEST_HOOK_STALL 1
+int mqs_set_test_hook(mqs_ctx* ctx, int32_t hook);
 
 /* Release a batch or a mesh (a mesh must have no live batch). */
 int mqs_free_batch(mqs_ctx* ctx, int32_t batch_id);

@@ -129,6 +129,7 @@ struct Ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int n_sm = 1;
+  int test_hook = 0;   // MQS_TEST_HOOK_* of mqs_set_test_hook
   std::vector<std::unique_ptr<MeshDev>> meshes;
   std::vector<std::unique_ptr<Batch>> batches;
   DevBuf mlmc;
@@ -655,8 +656,9 @@ int direct_cluster(const MeshDev& m, int lanes, int n_sm, const DirectConst& kc)
 
 // lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
 // vector in L2, several per SM (env MQS_DIRECT_WIDE=1/0 forces a choice).
-DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, bool mixed,
+DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, const Ctx& c, bool mixed,
                          double tol, int max_sweeps) {
+  const int n_sm = c.n_sm;
   DirectConst kc;
   memset(&kc, 0, sizeof(kc));
   kc.rowptr = m.rowptr.as<int32_t>();
@@ -679,7 +681,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, int n_sm, 
   kc.tol2 = tol * tol;
   kc.max_sweeps = max_sweeps;
   kc.cluster = direct_cluster(m, lanes, n_sm, kc);
-  kc.stall_test = env_int("MQS_TEST_STALL", 0) == 1 ? 1 : 0;
+  kc.stall_test = c.test_hook == MQS_TEST_HOOK_STALL ? 1 : 0;
   return kc;
 }
 
@@ -741,7 +743,7 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet* ff, in
   const int nf = ff ? b.n : 0, nc = fc ? b.n : 0;
   DirectSet& ds = b.dplain;
   MQS_TRY(ds.ensure(nf + nc, m.n_free));
-  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c.n_sm, mixed, tol, max_sweeps);
+  const DirectConst kc = direct_const(m, b, nf + nc, ctx->c, mixed, tol, max_sweeps);
   if (kc.cluster) {
     if (ff) MQS_TRY(ensure_couplings(ctx, b, m, *ff));
     if (fc) MQS_TRY(ensure_couplings(ctx, b, m, *fc));
@@ -797,8 +799,8 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
   MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.qraw.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.status.p, 0, (size_t)lanes * sizeof(int32_t), st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
-  const DirectConst kc = direct_const(m, b, lanes, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
-  const DirectConst kchain = direct_const(m, b, ns, ctx->c.n_sm, mixed, ir_tol, max_sweeps);
+  const DirectConst kc = direct_const(m, b, lanes, ctx->c, mixed, ir_tol, max_sweeps);
+  const DirectConst kchain = direct_const(m, b, ns, ctx->c, mixed, ir_tol, max_sweeps);
   if (kc.cluster && !fine_ready) MQS_TRY(ensure_couplings(ctx, b, m, fF));
   if (kchain.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fC));
   auto fine = [&](const DirectSet& d, int nl) -> int {
@@ -1231,7 +1233,7 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
         OnSide on(ctx->c);
         ff = factor_set(ctx, b, m, dt_level, mixed, rc);
         if (!ff) return rc;
-        const DirectConst kc = direct_const(m, b, b.n * n_slices, ctx->c.n_sm, mixed, cg_tol,
+        const DirectConst kc = direct_const(m, b, b.n * n_slices, ctx->c, mixed, cg_tol,
                                             cg_max_iters);
         if (kc.cluster) MQS_TRY(ensure_couplings(ctx, b, m, *ff));
         MQS_CUDA_TRY(cudaEventRecord(ctx->c.ev_join, ctx->c.side));
@@ -1574,6 +1576,16 @@ int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rms
   }
   if (estimate) *estimate = est;
   if (rmse) *rmse = std::sqrt(var_sum);
+  return MQS_OK;
+}
+
+int mqs_set_test_hook(mqs_ctx* ctx, int32_t hook) {
+  MQS_TRY(enter(ctx));
+  if (hook != 0 && hook != MQS_TEST_HOOK_STALL) {
+    set_error("unknown test hook %d", hook);
+    return MQS_EINVAL;
+  }
+  ctx->c.test_hook = hook;
   return MQS_OK;
 }
 

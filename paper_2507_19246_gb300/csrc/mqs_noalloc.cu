@@ -5,10 +5,10 @@
 //
 // Who needs it: code that must not allocate device memory while it runs --
 // for example a host application that hands the GPU to this library from a
-// real-time or signal-safe context, a runtime whose memory is fully carved up
-// by its own pool at start-up, or a caller that forbids allocation inside a
-// region it is recording.  Such callers pass their own inputs and outputs and
-// let the library work in this preallocated scratch.
+// real-time or signal-safe context (cudaMalloc may block or take locks), or a
+// runtime whose device memory is fully carved up by its own pool at start-up
+// (a cudaMalloc would fail or fight that pool).  Such callers pass their own
+// inputs and outputs and let the library work in this preallocated scratch.
 #include "mqs_internal.cuh"
 
 #include <algorithm>
@@ -73,6 +73,18 @@ __global__ void k_scale_qoi(const double* __restrict__ raw, int n_lanes, double 
 
 using namespace mqs;
 
+namespace {
+
+// Restores the calling thread's current device when the entry point returns.
+struct DeviceGuard {
+  int saved = -1;
+  ~DeviceGuard() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
+
+}  // namespace
+
 extern "C" int mqs_propagate_noalloc(int32_t device, void* cuda_stream, int32_t n,
                                      const int32_t* rowptr, const int32_t* colidx, int64_t nnz,
                                      int32_t n_lanes, const double* A, const double* M,
@@ -132,6 +144,8 @@ extern "C" int mqs_propagate_noalloc(int32_t device, void* cuda_stream, int32_t 
               off, kScratchBytes);
     return MQS_EINVAL;
   }
+  DeviceGuard guard;
+  MQS_CUDA_TRY(cudaGetDevice(&guard.saved));
   MQS_CUDA_TRY(cudaSetDevice(device));
   unsigned char* base = nullptr;
   MQS_TRY(scratch_address(device, &base));

@@ -23,6 +23,7 @@ MQS_FP64, MQS_MIXED = 0, 1
 MQS_QOI_ENERGY, MQS_QOI_JOULE = 0, 1
 MQS_ST_NOTCONV, MQS_ST_NONFINITE, MQS_ST_NOTSPD, MQS_ST_TIMEOUT = 1, 2, 4, 8
 MQS_SOLVER_PCG, MQS_SOLVER_BANDED = 0, 1
+MQS_TEST_HOOK_STALL = 1
 
 _lib = None
 _P = C.c_void_p
@@ -54,6 +55,7 @@ _SIGS = {
     "mqs_propagate_noalloc": (C.c_int, [_i32, _P, _i32, _P, _P, _i64, _i32, _P, _P, _P, _P, _i32,
                                         _P, _P, _P, _f64, _f64, _i32, _f64, _i32, _f64, _i32, _P,
                                         _P, _P]),
+    "mqs_set_test_hook": (C.c_int, [_P, _i32]),
     "mqs_free_batch": (C.c_int, [_P, _i32]),
     "mqs_free_mesh": (C.c_int, [_P, _i32]),
 }
@@ -245,6 +247,10 @@ def mqs_propagate_noalloc(device, stream, n, rowptr, colidx, nnz, n_lanes, A, M,
         qoi_kind, cg_tol, cg_max_iters, _ptr(a_out), _ptr(qoi_out), _ptr(status_out)))
 
 
+def mqs_set_test_hook(ctx, hook):
+    _check("mqs_set_test_hook", load().mqs_set_test_hook(ctx, int(hook)))
+
+
 def mqs_free_batch(ctx, batch):
     _check("mqs_free_batch", load().mqs_free_batch(ctx, batch))
 
@@ -344,6 +350,9 @@ class Context:
     def profile_read(self):
         """[launches, step-kernel launches, ms, sweep-kernel launches, ms]"""
         return mqs_profile_read(self.h)
+
+    def set_test_hook(self, hook):
+        mqs_set_test_hook(self.h, hook)
 
     def free_batch(self, batch):
         mqs_free_batch(self.h, batch)

@@ -100,3 +100,61 @@ def test_dirichlet_elimination_and_source():
     # sum r = J0 * conductor area (all conductor nodes are interior nodes)
     r = d.source(1.0 / 200.0)
     assert r.sum() == pytest.approx(p[4] * 0.25 ** 2, rel=1e-12)
+
+
+class _Patch:
+    """A hand-built mesh: four triangles, two source phases, one unwound
+    triangle (src_phase -1), node 5 touched by no source triangle."""
+    xy = np.array([[0.0, 0.0], [2.0, 0.0], [2.0, 1.0], [0.0, 3.0], [4.0, 0.0], [5.0, 5.0]])
+    tri = np.array([[0, 1, 2], [0, 2, 3], [1, 4, 2], [2, 4, 5]], dtype=np.int32)
+    n_nodes = 6
+    n_tri = 4
+    n_phases = 2
+    # |T| = 1, 3, 1, 3 (shoelace, by hand)
+    src_phase = np.array([0, 0, 1, -1], dtype=np.int32)
+    src_coef = np.array([1.0, 0.5, -1.0, 7.0])
+
+
+def test_load_vectors_node_by_node():
+    """Eq. 5 with P1 test functions: each vertex of a source triangle T gets
+    coef_T |T| / 3, summed over the triangles that share it.  Values worked
+    out by hand for _Patch."""
+    F = fem.full_load_vectors(_Patch)
+    third = 1.0 / 3.0
+    expect0 = [third + 0.5, third, third + 0.5, 0.5, 0.0, 0.0]   # T0 (coef 1, |T| 1), T1 (0.5, 3)
+    expect1 = [0.0, -third, -third, 0.0, -third, 0.0]            # T2 (coef -1, |T| 1)
+    assert F.shape == (2, 6)
+    assert np.allclose(F[0], expect0, rtol=1e-15, atol=1e-16)
+    assert np.allclose(F[1], expect1, rtol=1e-15, atol=1e-16)
+
+
+def test_load_vector_single_skewed_triangle():
+    class Tri:
+        xy = np.array([[0.0, 0.0], [3.0, 0.5], [1.0, 2.0]])   # |T| = |3*2 - 1*0.5| / 2 = 2.75
+        tri = np.array([[2, 0, 1]], dtype=np.int32)            # vertex order does not matter
+        n_nodes = 3
+        n_tri = 1
+        n_phases = 1
+        src_phase = np.array([0], dtype=np.int32)
+        src_coef = np.array([-1.5])
+    F = fem.full_load_vectors(Tri)
+    assert np.allclose(F[0], [-1.375, -1.375, -1.375], rtol=1e-15, atol=0)
+
+
+def test_three_phase_currents_by_hand():
+    """J_p(t) = J0 amp_p sin(2 pi f t - 2 pi p / 3 + phase_p) with P = 3 and
+    nonzero phase shifts (radians), evaluated by hand at two instants:
+      t = 1/600 s (2 pi f t = pi/6): arguments pi/2, 0, -pi/2;
+      t = 1/200 s (2 pi f t = pi/2): arguments 5pi/6, pi/3, -pi/6."""
+    m = meshes.annulus("5k")
+    R = m.n_regions
+    assert m.n_phases == 3
+    J0, amp, ph = 2.0, [1.0, 0.9, 1.1], [np.pi / 3, np.pi / 2, 2 * np.pi / 3]
+    p = np.concatenate([np.ones(R), np.ones(R), [J0], amp, ph])
+    d = fem.Discretisation(m, p, freq_hz=50.0)
+    assert np.allclose(d.phase_currents(1.0 / 600.0), [2.0, 0.0, -2.2], rtol=0, atol=1e-14)
+    assert np.allclose(d.phase_currents(1.0 / 200.0), [1.0, 0.9 * np.sqrt(3.0), -1.1],
+                       rtol=0, atol=1e-14)
+    # r(t) = sum_p J_p(t) F_p: at t = 1/600 s only phases 0 and 2 contribute
+    r = d.source(1.0 / 600.0)
+    assert np.allclose(r, 2.0 * d.F[0] - 2.2 * d.F[2], rtol=1e-14, atol=1e-14 * np.abs(r).max())

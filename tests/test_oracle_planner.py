@@ -73,3 +73,48 @@ def test_finite_core_speedup_limits():
     # few cores: level 0 needs many batches and the speedup collapses towards 1
     s_small = planner.speedup_nc([10303, 85, 10], 10, 2, 180)
     assert 1.0 < s_small < planner.speedup_inf(10, 2)
+
+
+def test_effort_increase_is_one_without_finest_samples():
+    """Eq. 18-19, 23: with N_L = 0 the combined and the plain MLMC effort are
+    the same sum over the coarser levels, so eps_inf = 1 whatever K and M."""
+    N, C = [40, 7, 0], [1.0, 10.0, 100.0]
+    for K, M in ((1, 4), (3, 16), (16, 16)):
+        assert planner.effort_increase_inf(N, C, K, M) == pytest.approx(1.0, rel=1e-15)
+
+
+def test_effort_increase_is_one_for_one_iteration_and_free_coarse_propagator():
+    """Eq. 16 with K = 1 and tau_C = 0 leaves E_para = (M-1)/M tau_F + tau_F/M
+    = tau_F, the sequential cost: one fine sweep over all slices.  With
+    tau_C = C_{L-2} = C_0 = 0, eps_inf = 1."""
+    N, C = [5, 3, 2], [0.0, 7.0, 50.0]
+    for M in (2, 8, 64):
+        assert planner.effort_para(1, M, 50.0, 0.0) == pytest.approx(50.0, rel=1e-15)
+        assert planner.effort_increase_inf(N, C, 1, M) == pytest.approx(1.0, rel=1e-15)
+
+
+def test_effort_increase_worked_case():
+    """r = 10, L = 2: C = (1, 10, 100), N = (100, 10, 2), K = 2, M = 16,
+    tau_F = C_2 = 100, tau_C = C_0 = 1.  By hand, from Eq. 14 per iteration:
+      k = 1: 16/16 * 100 + 15/16 * 1 = 100.9375
+      k = 2: 15/16 * 100 + 14/16 * 1 =  94.625      -> E_para = 195.5625
+    E_comb = 100*1 + 10*10 + 2*195.5625 = 591.125 (Eq. 19)
+    E_ref  = 100*1 + 10*10 + 2*100      = 400     (Eq. 17)
+    eps_inf = 591.125 / 400 = 4729/3200."""
+    N, C = [100, 10, 2], [1.0, 10.0, 100.0]
+    assert planner.effort_para(2, 16, 100.0, 1.0) == 195.5625
+    assert planner.effort_comb_inf(N, C, 195.5625) == 591.125
+    assert planner.effort_ref_inf(N, C) == 400.0
+    assert planner.effort_increase_inf(N, C, 2, 16) == pytest.approx(4729.0 / 3200.0, rel=1e-15)
+
+
+def test_combined_time_worked_case():
+    """Eq. 15 and 18, by hand: C = (1, 10, 100), K = 1, M = 16:
+    tau_para = 1/16 (100 + 15 * 1) = 7.1875 and tau_comb = 1 + 10 + 7.1875.
+    K = M = 16: tau_para = 100 + 7.5 * 1 (the serial fine cost plus the
+    coarse sweeps that Parareal adds when it does not converge early)."""
+    C = [1.0, 10.0, 100.0]
+    assert planner.tau_para(1, 16, 100.0, 1.0) == 7.1875
+    assert planner.tau_comb_inf(C, 7.1875) == 18.1875
+    assert planner.tau_para(16, 16, 100.0, 1.0) == 107.5
+    assert planner.tau_ref_inf(C) == 111.0
