@@ -33,6 +33,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# before CUDA initialises: hardware queues for the pipelined Parareal streams
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
@@ -175,58 +177,130 @@ def banded_flops(n_free, nnz, bw, lane_steps):
     return lane_steps * (subst + n_free * (2.0 * nnz / n_free + 10.0))
 
 
-# FP64 peak of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
-# ------------------------------------------------------------------ oracle arm
-ORACLE_SNIPPET = r"""
-import json, sys, time
-sys.path.insert(0, {root!r})
-import numpy as np
-from oracle import fem, stepper
-from workloads import meshes, params, configs
-mesh = meshes.{mesh_fn}
-p = {params_expr}
-n_steps = {n_steps}
-t0 = time.perf_counter()
-d = fem.Discretisation(mesh, p[0])
-prop = stepper.ImplicitEuler(d, {dt!r})
-a, raw, _ = prop.run(np.zeros(d.n), n_steps, qoi={qoi})
-el = time.perf_counter() - t0
-print(json.dumps({{"seconds": el, "units": n_steps * d.n}}))
-"""
+# FP64 peak from the unit counts (fallback when the in-tree measurement is
+# unavailable): 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def oracle_sample(wl, n_steps):
-    """Time the oracle's serial fine propagator on `n_steps` steps of the
-    workload's first sample in a single-threaded subprocess."""
-    mesh_fn = {"parareal_annulus20k": "annulus('20k')", "parareal_annulus20k_short": "annulus('20k')",
-               "mlmc_annulus20k": "annulus('20k')", "mlmc_annulus20k_short": "annulus('20k')",
-               "mc_square16": "unit_square(16)"}[wl["name"]]
-    params_expr = ("params.annulus_nominal(1)" if wl["name"].startswith("parareal")
-                   else "params.annulus_samples(1, 0)" if wl["name"].startswith("mlmc")
-                   else "params.square_samples(1)")
-    code = ORACLE_SNIPPET.format(root=ROOT, mesh_fn=mesh_fn, params_expr=params_expr,
-                                 n_steps=n_steps, dt=wl["dt"], qoi=wl["qoi"])
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         check=True)
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return r["units"] / r["seconds"], r["seconds"]
+# ------------------------------------------------------------------ oracle on the host cores
+# The oracle is plain FP64 numpy/scipy.  A spawn pool of one process per host
+# core runs its independent pieces: the fine propagations of one Parareal
+# iteration (the slices, as the method distributes them over cores) and the
+# level pairs of MLMC samples.  Each worker builds its propagators once.
+_W = {}
 
 
-def static_config(wl, args, n_free, nnz):
-    """The workload part of the JSON line's config, shared by both arms."""
+def _mesh_of(name):
+    from workloads import meshes
+    if name not in _W.setdefault("meshes", {}):
+        _W["meshes"][name] = (meshes.unit_square(16) if name == "square16"
+                              else meshes.annulus(name.replace("annulus", "")))
+    return _W["meshes"][name]
+
+
+def _init_fine(mesh_name, prow, dt, steps_per_slice, qoi):
+    from oracle import fem, stepper
+    d = fem.Discretisation(_mesh_of(mesh_name), prow)
+    _W["fine"] = (stepper.ImplicitEuler(d, dt), steps_per_slice, qoi)
+
+
+def _fine_task(task):
+    s, u = task
+    prop, S, qoi = _W["fine"]
+    a, raw, _ = prop.run(u, S, k0=s * S, qoi=qoi)
+    return a, raw
+
+
+def _pair_task(task):
+    """(Q_l, Q_{l-1}) of one sample from a(0) = 0 over `periods` periods."""
+    from oracle import mlmc
+    from workloads import configs
+    mesh_name, prow, level, periods, qoi = task
+    return mlmc.level_pair(_mesh_of(mesh_name), prow, level, configs.level_dt,
+                           lambda k: configs.level_steps(periods, k), qoi)
+
+
+def _serial_task(task):
+    """Serial implicit Euler of one sample for n_steps (MC workload)."""
+    from oracle import stepper
+    mesh_name, prow, dt, n_steps, qoi = task
+    q, _, _ = stepper.solve_sample(_mesh_of(mesh_name), prow, dt, n_steps, qoi)
+    return q
+
+
+def _init_worker(ready, init, initargs):
+    if init is not None:
+        init(*initargs)
+    with ready.get_lock():
+        ready.value += 1
+
+
+class OraclePool:
+    """One spawn process per host core; returns once every worker has run its
+    initializer (so that set-up is not timed)."""
+
+    def __init__(self, init=None, initargs=()):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = os.cpu_count() or 1
+        # one process per core, each single-threaded (the children read these
+        # when they import numpy)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        ready = ctx.Value("i", 0)
+        self.pool = ctx.Pool(processes=self.cores, initializer=_init_worker,
+                             initargs=(ready, init, initargs))
+        t0 = time.time()
+        while ready.value < self.cores and time.time() - t0 < 600:
+            time.sleep(0.05)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_parareal_pool(wl):
+    S = wl["n_steps"] // wl["n_slices"]
+    return OraclePool(_init_fine, (wl["mesh"].name, wl["params"][0], wl["dt"], S, wl["qoi"]))
+
+
+def oracle_parareal(wl, pool):
+    """The oracle's Parareal on the workload's sample with the fine slices of
+    each iteration on the pool's processes; returns (seconds, result).  The
+    workers' fine factorisations were built with the pool; the main process
+    builds its discretisation and the coarse factor inside the timed solve."""
+    from oracle import fem, parareal
+
+    def fmap(slices, starts):
+        return pool.pool.map(_fine_task, list(zip(slices, starts)))
+
+    t0 = time.perf_counter()
+    d = fem.Discretisation(wl["mesh"], wl["params"][0])
+    ref = parareal.parareal_sample(d, wl["dt"], wl["n_steps"], wl["n_slices"], wl["cf"],
+                                   wl["par_tol"], wl["qoi"], fine_map=fmap)
+    return time.perf_counter() - t0, ref
+
+
+def oracle_pairs(tasks, pool):
+    """Level pairs of MLMC samples on the pool: (seconds, results)."""
+    t0 = time.perf_counter()
+    out = pool.pool.map(_pair_task, tasks, chunksize=1)
+    return time.perf_counter() - t0, out
+
+
+def static_config(wl, args, n_free, nnz, world=1):
+    """The workload part of the JSON line's config, the same in both arms."""
     if "mlmc" in wl:
         c = wl["mlmc"]
         return {"workload": wl["name"], "n_free": n_free, "levels": len(c.n_per_level),
                 "n_per_level": list(c.n_per_level), "periods": c.periods,
                 "solver": args.solver, "precision": args.precision,
-                "solve_steps": c.solve_steps()}
+                "solve_steps": c.solve_steps(), "parallelism": f"replicas x{world}"}
     return {"workload": wl["name"], "mesh": wl["mesh"].name, "n_free": n_free, "nnz": nnz,
             "samples": int(wl["params"].shape[0]), "steps": wl["n_steps"], "dt": wl["dt"],
             "slices": wl["n_slices"], "coarse_factor": wl["cf"], "parareal_tol": wl["par_tol"],
-            "precision": args.precision, "solver": args.solver}
+            "precision": args.precision, "solver": args.solver,
+            "parallelism": f"replicas x{world}"}
 
 
 def mesh_pattern(mesh):
@@ -243,31 +317,63 @@ def mesh_pattern(mesh):
     return len(free), len(pairs)
 
 
+def mlmc_subset(c, n_each=2):
+    """Per-level sample subset of the MLMC workload: the first n_each samples
+    of every level (the level-pair QoIs the GPU run is checked against)."""
+    return [(l, j) for l in range(c.n_levels) for j in range(min(n_each, c.n_per_level[l]))]
+
+
 def run_reference(args, wl, rank, world):
+    """The oracle on the host cores, timed on the same workload as the GPU arm."""
     if rank != 0:
         return
-    # a bounded sample of serial fine steps: the Parareal sample's fine step,
-    # the MLMC workload's level-0 step, or the whole small MC run
-    n_steps = 256 if wl["name"].startswith(("parareal", "mlmc")) else wl["n_steps"]
-    total = wl["n_steps"] if wl["n_steps"] else wl["mlmc"].solve_steps()
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, _ = oracle_sample(wl, n_steps)
-        if i >= args.warmup:
-            vals.append(v)
+    n_free, nnz = mesh_pattern(wl["mesh"])
+    vals, secs = [], []
+    if "mlmc" in wl:
+        c = wl["mlmc"]
+        sub = mlmc_subset(c)
+        units = sum((c.steps(l) + (c.steps(l - 1) if l else 0)) for l, _ in sub) * n_free
+        what = (f"level pairs of {len(sub)} samples (the first 2 of each level) of the MLMC "
+                f"workload, serial implicit Euler with banded Cholesky per sample")
+        pool = OraclePool()
+        tasks = [(wl["mesh"].name, wl["params"][l][j], l, c.periods, c.qoi) for l, j in sub]
+        run = lambda: oracle_pairs(tasks, pool)[0]
+    elif wl["n_slices"] > 1:
+        units = wl["n_steps"] * n_free
+        what = (f"the oracle's Parareal of the workload ({wl['n_slices']} slices, tolerance "
+                f"{wl['par_tol']:g}): the fine slices of each iteration on the pool's "
+                f"processes, the coarse sweep and the Eq. 12 correction in the main process")
+        pool = oracle_parareal_pool(wl)
+        run = lambda: oracle_parareal(wl, pool)[0]
+    else:
+        units = wl["n_steps"] * n_free * wl["params"].shape[0]
+        what = "every sample of the workload, serial implicit Euler with banded Cholesky"
+        pool = OraclePool()
+        tasks = [(wl["mesh"].name, row, wl["dt"], wl["n_steps"], wl["qoi"]) for row in wl["params"]]
+
+        def run():
+            t0 = time.perf_counter()
+            pool.pool.map(_serial_task, tasks)
+            return time.perf_counter() - t0
+    try:
+        for i in range(args.warmup + args.steps):
+            t = run()
+            if i >= args.warmup:
+                vals.append(units / t)
+                secs.append(t)
+    finally:
+        pool.close()
+    cores = pool.cores
     value = statistics.median(vals)
-    sample = (f"serial fine implicit-Euler propagator of the oracle, {n_steps} of the "
-              f"workload's {total} sample-steps (first sample, level-0 step size for MLMC) "
-              f"per bench step, 1 thread")
     line = {"impl": "reference", "metric": "sample-DoF-steps/s", "value": value,
             "unit": "sample-DoF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": static_config(wl, args, *mesh_pattern(wl["mesh"])),
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": static_config(wl, args, n_free, nnz, world),
             "e2e": {"value": value, "unit": "sample-DoF-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
-            "cpu_baseline": {"value": value, "unit": "sample-DoF-steps/s", "cores": 1,
-                             "kind": "oracle", "sample": sample}}
+            "cpu_baseline": {"value": value, "unit": "sample-DoF-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": what + f"; {cores} host cores"}}
     print(json.dumps(line), flush=True)
 
 
@@ -297,15 +403,18 @@ def run_ours(args, wl, rank, world, dist):
     max_lin = (12 if mixed else 1) if args.solver == "banded" else 20000
     q_host = torch.zeros((ns, 2), dtype=torch.float64).pin_memory()
     flush = torch.empty(int(512e6) // 4, dtype=torch.float32, device=f"cuda:{dev}")
-    lanes_per_value = 1
+    # measured FP64 / FP32 peaks of this GPU (in-tree FMA-chain microbenchmark)
+    peak64 = mqs.mqs_measure_peak(dev, stream.cuda_stream, mqs.MQS_FP64)
+    peak32 = mqs.mqs_measure_peak(dev, stream.cuda_stream, mqs.MQS_MIXED)
 
-    def one_step(params_src, qoi_dst):
+    def one_step(params_src, qoi_dst, n_slices=None):
         b = mqs.mqs_set_samples(ctx.h, mesh_id, params_src)
         if args.solver == "banded":
             mqs.mqs_set_solver(ctx.h, b, mqs.MQS_SOLVER_BANDED)
         mqs.mqs_set_time(ctx.h, b, 0.0, wl["t_end"], 50.0, wl["qoi"])
-        k = mqs.mqs_propagate(ctx.h, b, 0, wl["dt"], 0.0, wl["n_slices"], wl["cf"],
-                              wl["n_slices"], wl["par_tol"], prec, tol_lin, max_lin)
+        m = wl["n_slices"] if n_slices is None else n_slices
+        k = mqs.mqs_propagate(ctx.h, b, 0, wl["dt"], 0.0, m, wl["cf"] if m > 1 else 1,
+                              m, wl["par_tol"], prec, tol_lin, max_lin)
         mqs.mqs_mlmc_accumulate(ctx.h, b, 0)
         mqs.mqs_read_qoi(ctx.h, b, qoi_dst)
         st = mqs.mqs_read_stats(ctx.h, b)
@@ -359,47 +468,36 @@ def run_ours(args, wl, rank, world, dist):
     value = world * units * args.steps / (ms_total / 1e3)
     e2e_value = world * units * len(e2e_times) / (e2e_total / 1e3)
     if rank != 0:
+        ctx.close()
         return
     st = stats[-1]
-    # roofline of the dominant kernel (stepping kernel vs coarse sweep), from the
-    # live CUDA-event timings of the timed region and the bytes model
+    # ---- roofline of the dominant kernel from the live CUDA-event timings of
+    # the timed region: the stepping kernel (Parareal fine chunks, several in
+    # flight on their own streams) against the time at least one of them ran
     step_ms, step_n, sweep_ms, sweep_n = prof[2], prof[1], prof[4], prof[3]
-    lpv = 1
-    if wl["n_slices"] > 1:
-        # Parareal fine lanes share one sample's values per tile
-        lpv = 32 if wl["n_slices"] % 32 == 0 else wl["n_slices"]
+    step_cov, sweep_cov = prof[5], prof[6]
+    bw = mqs.mqs_mesh_bandwidth(ctx.h, mesh_id) if args.solver == "banded" else 0
+    if args.solver == "banded":
+        step_flops = sum(banded_flops(n_free, nnz, bw, s[6]) for s in stats)
+        sweep_flops = sum(banded_flops(n_free, nnz, bw, s[7]) for s in stats)
+    else:
+        step_flops = sum(algorithmic_flops(n_free, nnz, s[4], s[6]) for s in stats)
+        sweep_flops = sum(algorithmic_flops(n_free, nnz, s[5], s[7]) for s in stats)
+    lpv = 32 if wl["n_slices"] % 32 == 0 else wl["n_slices"]
     step_bytes = sum(algorithmic_bytes(n_free, nnz, s[4], s[6], lpv, args.precision)
                      for s in stats)
-    sweep_bytes = sum(algorithmic_bytes(n_free, nnz, s[5], s[7], 1, args.precision) for s in stats)
-    peaks, peak_kind = _peaks()
-    dominant = "stepping" if step_ms >= sweep_ms else "coarse_sweep"
-    d_ms, d_n, d_bytes = (step_ms, step_n, step_bytes) if dominant == "stepping" else \
-        (sweep_ms, sweep_n, sweep_bytes)
-    if args.solver == "banded":
-        bw = mqs.mqs_mesh_bandwidth(ctx.h, mesh_id)
-        d_flops = sum(banded_flops(n_free, nnz, bw, s[6] if dominant == "stepping" else s[7])
-                      for s in stats)
-    else:
-        d_flops = sum(algorithmic_flops(n_free, nnz, s[4], s[6]) if dominant == "stepping" else
-                      algorithmic_flops(n_free, nnz, s[5], s[7]) for s in stats)
-    hbm_gbs = (d_bytes / max(d_n, 1)) / (d_ms / max(d_n, 1) / 1e3) / 1e9 if d_ms > 0 else 0.0
-    if args.precision == "fp64":
-        # the FP64 Jacobi-PCG works out of L2 and is bound by the FP64 pipe
-        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-        achieved = (d_flops / max(d_n, 1)) / (d_ms / max(d_n, 1) / 1e3) / 1e12 if d_ms > 0 else 0.0
-        peak_kind = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
-    else:
-        bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
-        achieved = hbm_gbs
-    # DRAM traffic per launch from a recorded ncu capture of the same kernel
-    # source (keyed by workload, precision, solver and kernel; null once the
-    # source file of that kernel has changed since the capture)
-    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    peaks, _ = _peaks()
+    peak_fp = peak64 if args.precision == "fp64" else peak32
+    dominant = "stepping" if step_cov >= sweep_cov else "coarse_sweep"
+    d_flops, d_cov = (step_flops, step_cov) if dominant == "stepping" else (sweep_flops, sweep_cov)
+    achieved = d_flops / (d_cov / 1e3) / 1e12 if d_cov > 0 else 0.0
+    # DRAM traffic per launch from a recorded single-pass ncu capture of the
+    # same kernel source (null once that source file has changed)
     traffic = None
     try:
         import hashlib
         key = f"{wl['name']}:{args.precision}:{args.solver}:{dominant}"
-        tr = json.load(open(traffic_path)).get(key)
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(key)
         if tr:
             src = os.path.join(ROOT, "paper_2507_19246_gb300", "csrc", tr["source_file"])
             cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -407,14 +505,6 @@ def run_ours(args, wl, rank, world, dist):
                 traffic = tr["bytes_per_launch"]
     except Exception:
         traffic = None
-    # CPU baseline: the oracle's serial fine propagator on a bounded sample
-    cpu = None
-    if not args.no_cpu_baseline:
-        n_cpu = 768 if wl["name"].startswith("parareal") else wl["n_steps"]
-        cv, secs = oracle_sample(wl, n_cpu)
-        cpu = {"value": cv, "unit": "sample-DoF-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_cpu} of {wl['n_steps']} fine steps of the workload's sample, serial "
-                         f"implicit Euler with banded Cholesky ({secs:.1f} s, 1 thread)"}
     clocks = clk.summary()
     line = {
         "metric": "sample-DoF-steps/s", "value": value, "unit": "sample-DoF-steps/s",
@@ -422,33 +512,154 @@ def run_ours(args, wl, rank, world, dist):
         "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": dict(static_config(wl, args, n_free, nnz), linear_tol=tol_lin,
-                       parareal_iters=ks[-1],
-                       l2="flushed (512 MB write) before every timed step",
-                       parallelism=f"replicas x{world}"),
-        "p50_ms": statistics.median(times), "p99_ms": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
+        "config": static_config(wl, args, n_free, nnz, world),
+        "l2": "flushed (512 MB write) before every timed step",
+        "linear_tol": tol_lin, "parareal_iters": ks[-1], "bandwidth": bw,
+        "p50_ms": statistics.median(times),
+        "p99_ms": sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
         "time_to_solution_s": ms_total / args.steps / 1e3,
-        "cg_iters_per_lane_step": (st[0] / max(st[1], 1)),
         "effort_solve_steps": st[1], "serial_equivalent_solve_steps": st[2],
         "qoi": float(q[0, 0]),
         "e2e": {"value": e2e_value, "unit": "sample-DoF-steps/s",
                 "h2d_bytes_per_step": int(p_host.numel() * 8), "d2h_bytes_per_step": int(ns * 2 * 8)},
         "gpu_launches": launches,
-        "roofline": {"bound": bound, "kernel": dominant, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": peak_kind, "algorithmic_gbs": hbm_gbs,
-                     "kernel_ms": {"stepping": step_ms / args.steps, "coarse_sweep": sweep_ms / args.steps}},
-        "cpu_baseline": cpu,
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak_fp,
+                     "unit": "TFLOP/s", "frac": achieved / peak_fp if peak_fp else None,
+                     "traffic": traffic,
+                     "peak_source": ("measured in-tree: FP64 FMA chains on every SM "
+                                     "(mqs_measure_peak), " if args.precision == "fp64" else
+                                     "measured in-tree: FP32 FMA chains (mqs_measure_peak), ")
+                                    + f"unit-count figure {FP64_PEAK_DERIVED:.3f} TFLOP/s FP64",
+                     "achieved_over": "time during which at least one launch of the kernel ran",
+                     "kernel_ms_per_step": {
+                         "stepping_sum": step_ms / args.steps, "stepping_covered": step_cov / args.steps,
+                         "coarse_sweep_sum": sweep_ms / args.steps,
+                         "coarse_sweep_covered": sweep_cov / args.steps},
+                     "coarse_sweep_tflops": sweep_flops / (sweep_cov / 1e3) / 1e12 if sweep_cov else 0.0,
+                     "algorithmic_dram_gbs": step_bytes / (step_cov / 1e3) / 1e9 if step_cov else 0.0,
+                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "peaks_measured": {"fp64_tflops": peak64, "fp32_tflops": peak32},
         "clocks": clocks,
     }
+    # ---- the paper's Parareal speedup s (Sec. II-C): the GPU's own serial fine
+    # solve of the same sample against the Parareal solve
+    if wl["n_slices"] > 1 and not args.no_extras:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step(p_dev, q_dev, n_slices=1)
+        e1.record(stream)
+        e1.synchronize()
+        serial_ms = e0.elapsed_time(e1)
+        line["gpu_serial_fine_ms"] = serial_ms
+        line["parareal_speedup_vs_gpu_serial"] = serial_ms / statistics.median(times)
+    # ---- MLMC time-to-RMSE (configs' MLMC workload), FP64 and mixed
+    if not args.no_extras and wl["name"] == "parareal_annulus20k":
+        line["mlmc"] = mlmc_records(args, ctx, mqs, torch, stream)
+    # ---- CPU baseline: the oracle on the host cores (after the GPU work)
+    if not args.no_cpu_baseline and wl["n_slices"] > 1:
+        pool = oracle_parareal_pool(wl)
+        try:
+            secs, ref = oracle_parareal(wl, pool)
+        finally:
+            pool.close()
+        line["cpu_baseline"] = {
+            "value": units / secs, "unit": "sample-DoF-steps/s", "cores": pool.cores,
+            "kind": "oracle",
+            "sample": (f"one Parareal solve of the workload by the oracle ({ref['iters']} "
+                       f"iterations, {secs:.1f} s): fine slices of each iteration on "
+                       f"{pool.cores} host processes, coarse sweep and correction in the main "
+                       f"process")}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def mlmc_records(args, ctx, mqs, torch, stream):
+    """MLMC estimate (Eq. 9) of the configs' MLMC workload on the 20k annulus
+    (4 levels, N_l = 4096/1024/256/64, 4 periods) in FP64 and in mixed
+    precision: time-to-RMSE (one timed estimate each after a one-level
+    warm-up), throughput, and the QoI error of the level pairs of a per-level
+    sample subset against the FP64 oracle."""
+    import numpy as np
+
+    from workloads import configs
+    wl = workload("mlmc20k")
+    c = wl["mlmc"]
+    mesh_id = ctx.upload_mesh(wl["mesh"])
+    n_free, _ = ctx.mesh_info(mesh_id)
+    p_dev = [torch.from_numpy(p).cuda() for p in wl["params"]]
+    sub = mlmc_subset(c)
+    chunk = 1024
+    out = {"workload": wl["name"], "n_per_level": list(c.n_per_level), "periods": c.periods,
+           "repeats": 1, "subset": "first 2 samples of every level"}
+
+    def estimate(prec, tol, sweeps, levels=None):
+        mqs.mqs_mlmc_reset(ctx.h, c.n_levels)
+        qsub = {}
+        for l, N in enumerate(c.n_per_level):
+            if levels is not None and l not in levels:
+                continue
+            for s0 in range(0, N, chunk):
+                b = mqs.mqs_set_samples(ctx.h, mesh_id, p_dev[l][s0:s0 + chunk])
+                mqs.mqs_set_solver(ctx.h, b, mqs.MQS_SOLVER_BANDED)
+                mqs.mqs_set_time(ctx.h, b, 0.0, wl["t_end"], 50.0, wl["qoi"])
+                mqs.mqs_propagate(ctx.h, b, l, configs.level_dt(l),
+                                  configs.level_dt(l - 1) if l else 0.0, 1, 1, 1, 0.0, prec,
+                                  tol, sweeps)
+                mqs.mqs_mlmc_accumulate(ctx.h, b, l)
+                if s0 == 0:
+                    qd = torch.empty((min(N, chunk), 2), dtype=torch.float64, device="cuda")
+                    mqs.mqs_read_qoi(ctx.h, b, qd)
+                    qsub[l] = qd
+                mqs.mqs_free_batch(ctx.h, b)
+        return mqs.mqs_mlmc_readout(ctx.h, c.n_levels), qsub
+
+    runs = {}
+    for name, prec, tol, sweeps in (("fp64", mqs.MQS_FP64, 1e-12, 1),
+                                    ("mixed", mqs.MQS_MIXED, 1e-10, 12)):
+        estimate(prec, tol, sweeps, levels=[c.n_levels - 1])      # warm-up: the finest level
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            e0.record(stream)
+            (lv, est, rmse), qsub = estimate(prec, tol, sweeps)
+            e1.record(stream)
+            e1.synchronize()
+            wall = time.perf_counter() - t0
+        qs = {l: qsub[l].cpu().numpy() for l in qsub}
+        runs[name] = qs
+        out[name] = {"time_to_rmse_s": wall, "device_s": e0.elapsed_time(e1) / 1e3,
+                     "estimate": est, "rmse": rmse, "levels": lv.tolist(),
+                     "sample_dof_steps_per_s": c.solve_steps() * n_free / wall,
+                     "linear_tol": tol, "max_sweeps": sweeps, "clocks": clk.summary()}
+    # the oracle's level pairs of the subset, on the host cores
+    pool = OraclePool()
+    try:
+        secs, ref = oracle_pairs([(wl["mesh"].name, wl["params"][l][j], l, c.periods, c.qoi)
+                                  for l, j in sub], pool)
+    finally:
+        pool.close()
+    cores = pool.cores
+    for name in ("fp64", "mixed"):
+        errs = []
+        for (l, j), (qf, qc) in zip(sub, ref):
+            errs.append(abs(runs[name][l][j, 0] - qf) / abs(qf))
+            if l:
+                errs.append(abs(runs[name][l][j, 1] - qc) / abs(qc))
+        out[name]["qoi_max_rel_err_vs_oracle"] = float(max(errs))
+    out["oracle_subset_s"] = secs
+    out["oracle_cores"] = cores
+    out["mixed_over_fp64_throughput"] = (out["mixed"]["sample_dof_steps_per_s"] /
+                                         out["fp64"]["sample_dof_steps_per_s"])
+    return out
 
 
 def run_mlmc(args, wl):
     """One MLMC estimate (Eq. 9) per step: every level's samples, both solves
     of each level pair, moments, readout; time-to-RMSE from upload to readout."""
-    import numpy as np
     import torch
 
     from paper_2507_19246_gb300 import mqs
@@ -520,16 +731,18 @@ def main():
                              "mlmc20k_short"])
     ap.add_argument("--solver", default="banded", choices=["pcg", "banded"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the GPU serial solve and the MLMC FP64/mixed records")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
     wl = workload(args.workload)
-    if args.workload.startswith("mlmc20k") and args.impl != "reference":
-        run_mlmc(args, wl)
-        return
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.workload.startswith("mlmc20k"):
+        run_mlmc(args, wl)
         return
     if world > 1:
         import torch

@@ -182,13 +182,30 @@ int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats);
 
 /* Instrumentation.  mqs_profile(ctx, 1) clears and starts recording CUDA-event
  * timings around every launch of the two time-stepping kernels on the
- * context's stream; 0 stops.  mqs_profile_read fills out[5] (host):
+ * stream of each launch; 0 stops.  mqs_profile_read fills out[7] (host):
  *   [0] kernels launched by this library in this process since it was loaded
  *   [1] recorded launches / [2] their summed duration (ms) of the stepping kernel
  *   [3] recorded launches / [4] their summed duration (ms) of the coarse-sweep kernel
+ *   [5] / [6] time (ms) during which at least one stepping / coarse-sweep
+ *       launch ran (launches on several streams overlap, so this can be less
+ *       than the sum)
  * and synchronises the stream. */
 int mqs_profile(mqs_ctx* ctx, int32_t enable);
 int mqs_profile_read(mqs_ctx* ctx, double* out);
+/* Measured arithmetic peak of device `device` (restored as current device
+ * afterwards): fused multiply-add chains on every SM, timed with CUDA events on
+ * `cuda_stream` (NULL: default stream).  precision MQS_FP64 measures the FP64
+ * rate (the roofline of the FP64 stepping kernels), MQS_MIXED the FP32 rate.
+ * *tflops receives TFLOP/s (2 flop per FMA).  About 0.1 s; allocates and frees
+ * 8 bytes of device memory.  Instrumentation, not part of the method. */
+int mqs_measure_peak(int32_t device, void* cuda_stream, int32_t precision, double* tflops);
+
+/* Launch intervals of the recorded launches of one kind (0 stepping, 1
+ * coarse sweep): out[2 j], out[2 j + 1] = start and end (ms) of launch j
+ * relative to the mqs_profile(ctx, 1) call, for j < min(*count, max_launches);
+ * *count receives the number recorded.  Synchronises the stream. */
+int mqs_profile_trace(mqs_ctx* ctx, int32_t kind, double* out, int32_t max_launches,
+                      int32_t* count);
 
 /* Apply a sample's matrix: y[s] = X_s x[s] with X = M (which = 0), K (1) or
  * A = M/dt + K (2) for every sample s of the batch; x, y host or device,

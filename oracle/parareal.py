@@ -30,11 +30,16 @@ import math
 import numpy as np
 
 
-def parareal(fine, coarse, u0: np.ndarray, n_slices: int, tol: float, max_iter: int = None):
+def parareal(fine, coarse, u0: np.ndarray, n_slices: int, tol: float, max_iter: int = None,
+             fine_map=None):
     """Run Parareal.
 
     fine(s, u)   -> (u_end, qoi_partial)  fine propagation of slice s from u
     coarse(s, u) -> u_end                 coarse propagation of slice s from u
+    fine_map(slices, starts) -> [(u_end, qoi_partial)]: how the independent
+        fine propagations of one iteration are evaluated (default: one after
+        the other with `fine`; a process pool may run them on several cores,
+        as the method intends -- the arithmetic of each is the same)
     Returns dict(iters, a_end, qoi_raw, U (slice starts), jumps (per iteration),
                  fine_slices (fine solves executed), coarse_slices).
     """
@@ -54,8 +59,13 @@ def parareal(fine, coarse, u0: np.ndarray, n_slices: int, tol: float, max_iter: 
     n_fine = 0
     k = 0
     for k in range(1, max_iter + 1):
-        for s in range(k - 1, M):
-            E[s], q[s] = fine(s, U[s])
+        slices = list(range(k - 1, M))
+        if fine_map is None:
+            results = [fine(s, U[s]) for s in slices]
+        else:
+            results = fine_map(slices, [U[s] for s in slices])
+        for s, (e, qs) in zip(slices, results):
+            E[s], q[s] = e, qs
             n_fine += 1
         U_prev = [u.copy() for u in U]
         for s in range(k - 1, M - 1):
@@ -74,11 +84,14 @@ def parareal(fine, coarse, u0: np.ndarray, n_slices: int, tol: float, max_iter: 
 
 
 def parareal_sample(disc, dt_fine: float, n_steps: int, n_slices: int, coarse_factor: int,
-                    tol: float, qoi: int, t0: float = 0.0, max_iter: int = None):
+                    tol: float, qoi: int, t0: float = 0.0, max_iter: int = None,
+                    fine_map=None):
     """Parareal for one sample with implicit-Euler fine and coarse propagators.
 
     Slice s starts at global fine step s*S (S = n_steps / n_slices) and the
     coarse propagator takes S / coarse_factor steps of coarse_factor * dt_fine.
+    fine_map: see parareal(); it receives slice indices and start states and
+    must apply the same fine propagator (dt_fine, S steps from step s*S).
     """
     from .stepper import ImplicitEuler
     if n_steps % n_slices or (n_steps // n_slices) % coarse_factor:
@@ -96,4 +109,4 @@ def parareal_sample(disc, dt_fine: float, n_steps: int, n_slices: int, coarse_fa
         a, _, _ = coarse_p.run(u, Sc, k0=s * Sc, qoi=qoi)
         return a
 
-    return parareal(fine, coarse, np.zeros(disc.n), n_slices, tol, max_iter)
+    return parareal(fine, coarse, np.zeros(disc.n), n_slices, tol, max_iter, fine_map)

@@ -93,6 +93,30 @@ struct LaneSet {
   }
 };
 
+// Pinned host memory mapped into the device address space (written by
+// kernels, read by the host without a copy, and the reverse).
+struct MappedBuf {
+  void* h = nullptr;
+  void* d = nullptr;
+  size_t bytes = 0;
+  MappedBuf() = default;
+  MappedBuf(const MappedBuf&) = delete;
+  MappedBuf& operator=(const MappedBuf&) = delete;
+  ~MappedBuf() {
+    if (h) cudaFreeHost(h);
+  }
+  int ensure(size_t n) {
+    if (n <= bytes && h) return MQS_OK;
+    if (h) cudaFreeHost(h);
+    h = d = nullptr;
+    bytes = 0;
+    MQS_CUDA_TRY(cudaHostAlloc(&h, n, cudaHostAllocMapped));
+    MQS_CUDA_TRY(cudaHostGetDevicePointer(&d, h, 0));
+    bytes = n;
+    return MQS_OK;
+  }
+};
+
 struct Batch {
   int mesh_id = -1;
   int n = 0, n_params = 0;
@@ -118,6 +142,10 @@ struct Batch {
   std::vector<std::unique_ptr<FactorSet>> fsets;
   DirectSet dplain, dpar, dchain;
   DevBuf E;                                    // Parareal fine ends, lane-major
+  double* E_final = nullptr;                   // fine ends of the last Parareal iteration
+  DevBuf qraw2, pdesc;                         // pipelined Parareal: [2][lanes] QoI partials,
+                                               // [2][lanes] fine-lane descriptors
+  MappedBuf jhist, nhist, stop;                // per-iteration jump / norm squares, cancel word
   int nf_direct = 0;
 };
 
@@ -134,8 +162,14 @@ struct Ctx {
   std::vector<std::unique_ptr<Batch>> batches;
   DevBuf mlmc;
   int n_levels = 0;
-  // instrumentation: event pairs around the stepping (0) and coarse-sweep (1) launches
+  // pipelined Parareal: streams of the fine chunks and the events that order
+  // them against the sweep chunks ([iteration parity][chunk])
+  std::vector<cudaStream_t> fine_st;
+  std::vector<cudaEvent_t> ev_sweep[2], ev_fine[2], ev_fjoin;
+  // instrumentation: event pairs around the stepping (0) and coarse-sweep (1)
+  // launches, on the stream of each launch; t0 on the main stream when enabled
   bool prof = false;
+  cudaEvent_t prof_t0 = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
   size_t ev_used[2] = {0, 0};
   ~Ctx() {
@@ -144,14 +178,45 @@ struct Ctx {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
       }
+    if (prof_t0) cudaEventDestroy(prof_t0);
     if (side) {
       cudaStreamSynchronize(side);
       cudaStreamDestroy(side);
     }
+    for (cudaStream_t f : fine_st) {
+      cudaStreamSynchronize(f);
+      cudaStreamDestroy(f);
+    }
+    for (int p = 0; p < 2; ++p) {
+      for (cudaEvent_t e : ev_sweep[p]) cudaEventDestroy(e);
+      for (cudaEvent_t e : ev_fine[p]) cudaEventDestroy(e);
+    }
+    for (cudaEvent_t e : ev_fjoin) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
   }
 };
+
+// `chunks` streams for the fine chunks and the ordering events.
+int ensure_pipeline(Ctx& c, int chunks) {
+  while ((int)c.fine_st.size() < chunks) {
+    cudaStream_t f;
+    MQS_CUDA_TRY(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking));
+    c.fine_st.push_back(f);
+    cudaEvent_t e;
+    MQS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c.ev_fjoin.push_back(e);
+    for (int p = 0; p < 2; ++p) {
+      MQS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c.ev_sweep[p].push_back(e);
+      MQS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c.ev_fine[p].push_back(e);
+    }
+  }
+  return MQS_OK;
+}
+
+
 
 int ensure_side(Ctx& c) {
   if (!c.side) MQS_CUDA_TRY(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
@@ -168,9 +233,11 @@ struct OnSide {
   ~OnSide() { c.stream = saved; }
 };
 
-// Record the start (begin = true) or end event of a launch of kind k.
-int prof_mark(Ctx& c, int k, bool begin) {
+// Record the start (begin = true) or end event of a launch of kind k on
+// stream st (default: the context's stream).
+int prof_mark(Ctx& c, int k, bool begin, cudaStream_t st = nullptr) {
   if (!c.prof) return MQS_OK;
+  if (!st) st = c.stream;
   if (begin) {
     if (c.ev_used[k] == c.ev[k].size()) {
       cudaEvent_t a, b;
@@ -178,9 +245,9 @@ int prof_mark(Ctx& c, int k, bool begin) {
       MQS_CUDA_TRY(cudaEventCreate(&b));
       c.ev[k].emplace_back(a, b);
     }
-    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].first, c.stream));
+    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].first, st));
   } else {
-    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].second, c.stream));
+    MQS_CUDA_TRY(cudaEventRecord(c.ev[k][c.ev_used[k]].second, st));
     c.ev_used[k]++;
   }
   return MQS_OK;
@@ -775,6 +842,11 @@ int run_plain_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet* ff, in
   return MQS_OK;
 }
 
+int run_parareal_pipelined(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
+                           FactorSet& fC, int n_steps, int M, int max_iters, double tol,
+                           int& iters_out, cudaEvent_t fine_ready, const DirectConst& kc_in,
+                           const DirectConst& kchain_in);
+
 // fine_ready: event after which fF is complete (the fine factorisation ran on
 // the side stream), waited for before the first fine batch; null if fF is
 // already ordered on the main stream.
@@ -800,9 +872,16 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
   MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.status.p, 0, (size_t)lanes * sizeof(int32_t), st));
   MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
   const DirectConst kc = direct_const(m, b, lanes, ctx->c, mixed, ir_tol, max_sweeps);
-  const DirectConst kchain = direct_const(m, b, ns, ctx->c, mixed, ir_tol, max_sweeps);
+  DirectConst kchain = direct_const(m, b, ns, ctx->c, mixed, ir_tol, max_sweeps);
+  {   // env MQS_CHAIN_CLUSTER=1/2/4/8 forces the coarse sweep's cluster size
+    const int fc = env_int("MQS_CHAIN_CLUSTER", 0);
+    if (kchain.cluster && (fc == 1 || fc == 2 || fc == 4 || fc == 8)) kchain.cluster = fc;
+  }
   if (kc.cluster && !fine_ready) MQS_TRY(ensure_couplings(ctx, b, m, fF));
   if (kchain.cluster) MQS_TRY(ensure_couplings(ctx, b, m, fC));
+  if (kc.cluster && kchain.cluster && env_int("MQS_PARAREAL_PIPELINE", 1) != 0)
+    return run_parareal_pipelined(ctx, b, m, fF, fC, n_steps, M, max_iters, tol, iters_out,
+                                  fine_ready, kc, kchain);
   auto fine = [&](const DirectSet& d, int nl) -> int {
     return kc.cluster ? launch_cluster(d.desc.as<DirectLane>(), nl, kc, st)
                       : launch_direct(d.desc.as<DirectLane>(), nl, kc, st);
@@ -819,14 +898,15 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
                                   dc.status.as<int32_t>() + s, Sc, 0, 1));
   MQS_TRY(upload_direct(ctx, dc));
   DirectChain ch;
-  ch.U = b.U.as<double>();
+  ch.U_prev = ch.U_cur = b.U.as<double>();
   ch.E = b.E.as<double>();
   ch.G = b.G.as<double>();
   ch.M = M;
   ch.steps_per_slice = Sc;
   ch.jump2 = b.jump2.as<double>();
   ch.norm2 = b.norm2.as<double>();
-  ch.s_begin = 0;
+  ch.s_first = ch.s_begin = 0;
+  ch.s_end = M;
   ch.first_sweep = 1;
   MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
   MQS_TRY(prof_mark(ctx->c, 1, true));
@@ -856,7 +936,7 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
     MQS_TRY(prof_mark(ctx->c, 0, false));
     MQS_CUDA_TRY(cudaMemsetAsync(b.jump2.p, 0, (size_t)lanes * sizeof(double), st));
     if (k - 1 <= M - 2) {
-      ch.s_begin = k - 1;
+      ch.s_first = ch.s_begin = k - 1;
       ch.first_sweep = 0;
       MQS_TRY(prof_mark(ctx->c, 1, true));
       MQS_TRY(chain(ch));
@@ -882,6 +962,189 @@ int run_parareal_direct(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
     if (all || k >= M) break;
   }
   iters_out = std::min(k, max_iters);
+  b.E_final = b.E.as<double>();
+  b.stats[1] += exec_steps;
+  b.stats[2] += (double)ns * n_steps;
+  b.stats[6] += fine_steps;
+  b.stats[7] += chain_steps;
+  return MQS_OK;
+}
+
+// Parareal with the coarse sweep and the fine propagation overlapped (the
+// same arithmetic as run_parareal_direct, so bitwise the same results).  The
+// slices are cut into J chunks of c slices.  Iteration k's fine chunk j needs
+// only the slice starts that iteration k - 1's sweep wrote up to the end of
+// chunk j, and the sweep of chunk j needs only that chunk's fine ends, so
+//   fine(k, j)  waits for  sweep(k - 1, j)          (one stream per chunk)
+//   sweep(k, j) waits for  fine(k, j), sweep(k, j - 1)   (the main stream)
+// and the sweep of one chunk runs while later chunks still propagate.  Slice
+// starts and fine ends are double-buffered by iteration parity (U_k, E_k,
+// per-slice QoI partials), so iteration k + 1 can be enqueued before the host
+// knows whether iteration k met the stopping rule; per-iteration jump and norm
+// squares go to host-mapped memory, read once the last sweep chunk of
+// iteration k has run.  When iteration K stops, the host raises the
+// cancellation word (host-mapped) and the kernels of iteration K + 1 leave at
+// their next step boundary; the call drains them before it returns.
+// Cluster stepping kernels only (they carry the cancellation check).
+int run_parareal_pipelined(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& fF,
+                           FactorSet& fC, int n_steps, int M, int max_iters, double tol,
+                           int& iters_out, cudaEvent_t fine_ready, const DirectConst& kc_in,
+                           const DirectConst& kchain_in) {
+  Ctx& c = ctx->c;
+  const cudaStream_t st = c.stream;
+  const int S = n_steps / M, Sc = S / (int)std::lround(fC.dt / fF.dt), ns = b.n, n = m.n_free;
+  const int lanes = ns * M;
+  const int64_t field = (int64_t)lanes * n;
+  const int cs = std::max(1, M / 16);              // slices per chunk
+  const int J = (M + cs - 1) / cs;                 // chunks
+  MQS_TRY(ensure_pipeline(c, J));
+  MQS_TRY(b.U.ensure(2 * field * sizeof(double)));
+  MQS_TRY(b.E.ensure(2 * field * sizeof(double)));
+  MQS_TRY(b.G.ensure(field * sizeof(double)));
+  MQS_TRY(b.qraw2.ensure(2 * (size_t)lanes * sizeof(double)));
+  MQS_TRY(b.pdesc.ensure(2 * (size_t)lanes * sizeof(DirectLane)));
+  MQS_TRY(b.dpar.ensure(lanes, n));
+  MQS_TRY(b.dchain.ensure(ns, n));
+  const size_t hist = (size_t)(max_iters + 2) * lanes * sizeof(double);
+  MQS_TRY(b.jhist.ensure(hist));
+  MQS_TRY(b.nhist.ensure(hist));
+  MQS_TRY(b.stop.ensure(sizeof(int32_t)));
+  // nothing of an earlier call touches the mapped words any more: every
+  // pipelined call drains its cancelled kernels before it returns
+  memset(b.jhist.h, 0, hist);
+  memset(b.nhist.h, 0, hist);
+  volatile int32_t* stop_h = static_cast<volatile int32_t*>(b.stop.h);
+  *stop_h = INT32_MAX;
+  double* U0 = b.U.as<double>();
+  double* E0 = b.E.as<double>();
+  double* q2 = b.qraw2.as<double>();
+  MQS_CUDA_TRY(cudaMemsetAsync(U0, 0, 2 * field * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(q2, 0, 2 * (size_t)lanes * sizeof(double), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.dpar.status.p, 0, (size_t)lanes * sizeof(int32_t), st));
+  MQS_CUDA_TRY(cudaMemsetAsync(b.dchain.status.p, 0, (size_t)ns * sizeof(int32_t), st));
+  DirectConst kc = kc_in, kchain = kchain_in;
+  kc.stop = kchain.stop = static_cast<const volatile int32_t*>(b.stop.d);
+  // fine-lane descriptors of both parities, slice-major (chunk = contiguous range)
+  std::vector<DirectLane> pd((size_t)2 * lanes);
+  for (int par = 0; par < 2; ++par)
+    for (int j = 0; j < M; ++j)
+      for (int smp = 0; smp < ns; ++smp) {
+        const int l = smp * M + j;
+        DirectLane d = direct_lane(m, b, fF, smp, E0 + par * field + (int64_t)l * n,
+                                   b.dpar.v(l, 1), b.dpar.v(l, 2), b.dpar.v(l, 3),
+                                   b.dpar.v(l, 4), q2 + (size_t)par * lanes + l,
+                                   b.dpar.status.as<int32_t>() + l, S, (int64_t)j * S, 1);
+        d.a_init = U0 + (par ^ 1) * field + (int64_t)l * n;   // U of iteration k - 1
+        pd[(size_t)par * lanes + (size_t)j * ns + smp] = d;
+      }
+  MQS_CUDA_TRY(cudaMemcpyAsync(b.pdesc.p, pd.data(), pd.size() * sizeof(DirectLane),
+                               cudaMemcpyHostToDevice, st));
+  DirectSet& dc = b.dchain;
+  dc.host.clear();
+  for (int smp = 0; smp < ns; ++smp)
+    dc.host.push_back(direct_lane(m, b, fC, smp, dc.v(smp, 0), dc.v(smp, 1), dc.v(smp, 2),
+                                  dc.v(smp, 3), dc.v(smp, 4), dc.qraw.as<double>() + smp,
+                                  dc.status.as<int32_t>() + smp, Sc, 0, 1));
+  MQS_TRY(upload_direct(ctx, dc));
+  // the fine chunk streams start after everything enqueued so far
+  MQS_CUDA_TRY(cudaEventRecord(c.ev_fork, st));
+  for (int j = 0; j < J; ++j) MQS_CUDA_TRY(cudaStreamWaitEvent(c.fine_st[j], c.ev_fork, 0));
+  if (fine_ready)
+    for (int j = 0; j < J; ++j) MQS_CUDA_TRY(cudaStreamWaitEvent(c.fine_st[j], fine_ready, 0));
+  const DirectLane* dpd = b.pdesc.as<DirectLane>();
+  double* jh = static_cast<double*>(b.jhist.d);
+  double* nh = static_cast<double*>(b.nhist.d);
+  double exec_steps = 0.0, chain_steps = 0.0, fine_steps = 0.0;
+  // sweep of iteration k (k = 0: the initial coarse sweep), chunk by chunk
+  auto sweep = [&](int k) -> int {
+    const int pk = k & 1;
+    DirectChain ch;
+    ch.U_prev = U0 + (pk ^ 1) * field;
+    ch.U_cur = U0 + pk * field;
+    ch.E = E0 + pk * field;
+    ch.G = b.G.as<double>();
+    ch.M = M;
+    ch.steps_per_slice = Sc;
+    ch.jump2 = jh + (size_t)k * lanes;
+    ch.norm2 = nh + (size_t)k * lanes;
+    ch.s_first = k == 0 ? 0 : k - 1;
+    ch.first_sweep = k == 0 ? 1 : 0;
+    DirectConst kk = kchain;
+    kk.iter = k;
+    for (int j = 0; j < J; ++j) {
+      const int lo = std::max(j * cs, ch.s_first), hi = std::min((j + 1) * cs, M - 1);
+      if (k > 0) MQS_CUDA_TRY(cudaStreamWaitEvent(st, c.ev_fine[pk][j], 0));
+      if (lo < hi) {
+        ch.s_begin = lo;
+        ch.s_end = hi;
+        MQS_TRY(prof_mark(c, 1, true));
+        MQS_TRY(launch_cluster_chain(dc.desc.as<DirectLane>(), ns, kk, ch, st));
+        MQS_TRY(prof_mark(c, 1, false));
+      }
+      MQS_CUDA_TRY(cudaEventRecord(c.ev_sweep[pk][j], st));
+    }
+    return MQS_OK;
+  };
+  // fine propagation of iteration k >= 1 on slices k - 1 .. M - 1, chunk by chunk
+  auto fine = [&](int k) -> int {
+    const int pk = k & 1;
+    DirectConst kk = kc;
+    kk.iter = k;
+    for (int j = 0; j < J; ++j) {
+      const int lo = std::max(j * cs, k - 1), hi = std::min((j + 1) * cs, M);
+      const cudaStream_t fs = c.fine_st[j];
+      MQS_CUDA_TRY(cudaStreamWaitEvent(fs, c.ev_sweep[pk ^ 1][j], 0));
+      if (lo < hi) {
+        MQS_TRY(prof_mark(c, 0, true, fs));
+        MQS_TRY(launch_cluster(dpd + (size_t)pk * lanes + (size_t)lo * ns, (hi - lo) * ns, kk,
+                               fs));
+        MQS_TRY(prof_mark(c, 0, false, fs));
+      }
+      MQS_CUDA_TRY(cudaEventRecord(c.ev_fine[pk][j], fs));
+    }
+    return MQS_OK;
+  };
+  MQS_TRY(sweep(0));
+  int K = 0;
+  auto enqueue = [&](int k) -> int {
+    MQS_TRY(fine(k));
+    return sweep(k);
+  };
+  MQS_TRY(enqueue(1));
+  for (int k = 1; k <= max_iters; ++k) {
+    if (k + 1 <= max_iters && k < M) MQS_TRY(enqueue(k + 1));   // ahead, speculatively
+    MQS_CUDA_TRY(cudaEventSynchronize(c.ev_sweep[k & 1][J - 1]));
+    const double* hj = static_cast<const double*>(b.jhist.h) + (size_t)k * lanes;
+    bool all = true;
+    for (int smp = 0; smp < ns; ++smp) {
+      double num = 0.0, den = 0.0;
+      for (int j = 0; j < M; ++j) {
+        // the last iteration <= k that wrote slice start j is min(k, j)
+        const double* hn = static_cast<const double*>(b.nhist.h) + (size_t)std::min(k, j) * lanes;
+        num = std::max(num, std::sqrt(hj[(size_t)smp * M + j]));
+        den = std::max(den, std::sqrt(hn[(size_t)smp * M + j]));
+      }
+      const double jump = den > 0.0 ? num / den : num;
+      if (!(jump <= tol)) all = false;
+    }
+    K = k;
+    fine_steps += (double)ns * (M - (k - 1)) * S;
+    if (all || k >= M || k >= max_iters) break;
+  }
+  // cancel the iteration enqueued ahead (if any) and drain it
+  *stop_h = K;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  for (int j = 0; j < J; ++j) {
+    MQS_CUDA_TRY(cudaEventRecord(c.ev_fjoin[j], c.fine_st[j]));
+    MQS_CUDA_TRY(cudaStreamWaitEvent(st, c.ev_fjoin[j], 0));
+  }
+  MQS_TRY(gather_parareal_qraw(q2, lanes, M, K, b.dpar.qraw.as<double>(), st));
+  MQS_CUDA_TRY(cudaStreamSynchronize(st));
+  iters_out = K;
+  b.E_final = E0 + (K & 1) * field;
+  // sweeps of iterations 0..K (those of K + 1, enqueued ahead, were cancelled)
+  for (int k = 0; k <= K; ++k) chain_steps += (double)ns * (M - 1 - std::max(0, k - 1)) * Sc;
+  exec_steps = fine_steps + chain_steps;
   b.stats[1] += exec_steps;
   b.stats[2] += (double)ns * n_steps;
   b.stats[6] += fine_steps;
@@ -1025,7 +1288,15 @@ int mqs_upload_mesh(mqs_ctx* ctx, int32_t n_nodes, const double* xy, int32_t n_t
   // reverse Cuthill-McKee ordering and the lower-band position of each nonzero
   std::vector<int32_t> perm, iperm(m.n_free), band_idx(m.nnz);
   int32_t bw = 0;
-  rcm_order(m.n_free, rowptr, colidx, perm, bw);
+  std::vector<char> boundary(m.n_free, 0);   // free nodes sharing a triangle with a Dirichlet node
+  for (int64_t e = 0; e < n_tri; ++e) {
+    bool has_dir = false;
+    for (int a = 0; a < 3; ++a) has_dir |= fid[tri[3 * e + a]] < 0;
+    if (has_dir)
+      for (int a = 0; a < 3; ++a)
+        if (fid[tri[3 * e + a]] >= 0) boundary[fid[tri[3 * e + a]]] = 1;
+  }
+  rcm_order(m.n_free, rowptr, colidx, boundary, perm, bw);
   for (int32_t i = 0; i < m.n_free; ++i) iperm[perm[i]] = i;
   if ((int64_t)m.n_free * (bw + 1) >= (int64_t)INT32_MAX) bw = -1;   // too wide for the band solver
   for (int32_t i = 0; i < m.n_free; ++i)
@@ -1245,6 +1516,9 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
     }
     FactorSet* fc = nullptr;
     if (dt_prev > 0.0 && !(fc = factor_set(ctx, b, m, dt_prev, mixed, rc))) return rc;
+    // a step size equal to the fine one shares the fine factor, which the side
+    // stream may still be computing: the main stream waits for it first
+    if (fine_ready && fc == ff) MQS_CUDA_TRY(cudaStreamWaitEvent(ctx->c.stream, fine_ready, 0));
     b.level = level;
     b.has_coarse = fc != nullptr;
     for (double& x : b.stats) x = 0.0;
@@ -1264,6 +1538,8 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
         MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc, mixed, cg_tol, cg_max_iters));
       FactorSet* fC = factor_set(ctx, b, m, dt_level * coarse_factor, mixed, rc);
       if (!fC) return rc;
+      if (fine_ready && fC == ff)   // coarse_factor 1: the coarse sweep uses the fine factor
+        MQS_CUDA_TRY(cudaStreamWaitEvent(ctx->c.stream, fine_ready, 0));
       MQS_TRY(run_parareal_direct(ctx, b, m, *ff, *fC, nsf, n_slices, coarse_factor,
                                   max_par_iters, par_tol, mixed, cg_tol, cg_max_iters,
                                   par_iters, fine_ready));
@@ -1402,7 +1678,7 @@ int mqs_read_state(mqs_ctx* ctx, int32_t batch_id, int32_t which, double* a) {
     const double* src;
     size_t pitch;
     if (which == 0 && b->mode == 4) {
-      src = b->E.as<double>() + (size_t)(b->M - 1) * m.n_free;
+      src = b->E_final + (size_t)(b->M - 1) * m.n_free;
       pitch = row * b->M;
     } else {
       const int lane0 = which == 0 ? 0 : b->nf_direct;
@@ -1456,7 +1732,11 @@ int mqs_read_stats(mqs_ctx* ctx, int32_t batch_id, double* stats) {
 int mqs_profile(mqs_ctx* ctx, int32_t enable) {
   MQS_TRY(enter(ctx));
   ctx->c.prof = enable != 0;
-  if (enable) ctx->c.ev_used[0] = ctx->c.ev_used[1] = 0;
+  if (enable) {
+    ctx->c.ev_used[0] = ctx->c.ev_used[1] = 0;
+    if (!ctx->c.prof_t0) MQS_CUDA_TRY(cudaEventCreate(&ctx->c.prof_t0));
+    MQS_CUDA_TRY(cudaEventRecord(ctx->c.prof_t0, ctx->c.stream));
+  }
   return MQS_OK;
 }
 
@@ -1470,13 +1750,57 @@ int mqs_profile_read(mqs_ctx* ctx, double* out) {
   out[0] = (double)g_launches.load();
   for (int k = 0; k < 2; ++k) {
     double ms = 0.0;
+    std::vector<std::pair<double, double>> iv;
     for (size_t j = 0; j < ctx->c.ev_used[k]; ++j) {
-      float e = 0.0f;
+      float e = 0.0f, a = 0.0f, z = 0.0f;
+      MQS_CUDA_TRY(cudaEventSynchronize(ctx->c.ev[k][j].second));
       MQS_CUDA_TRY(cudaEventElapsedTime(&e, ctx->c.ev[k][j].first, ctx->c.ev[k][j].second));
       ms += e;
+      if (ctx->c.prof_t0) {
+        MQS_CUDA_TRY(cudaEventElapsedTime(&a, ctx->c.prof_t0, ctx->c.ev[k][j].first));
+        MQS_CUDA_TRY(cudaEventElapsedTime(&z, ctx->c.prof_t0, ctx->c.ev[k][j].second));
+        iv.emplace_back(a, z);
+      }
     }
+    // time covered by at least one launch of the kind (launches on several
+    // streams overlap)
+    std::sort(iv.begin(), iv.end());
+    double covered = 0.0, cur_a = 0.0, cur_z = -1.0;
+    for (const auto& x : iv) {
+      if (x.first > cur_z) {
+        if (cur_z > cur_a) covered += cur_z - cur_a;
+        cur_a = x.first;
+        cur_z = x.second;
+      } else {
+        cur_z = std::max(cur_z, x.second);
+      }
+    }
+    if (cur_z > cur_a) covered += cur_z - cur_a;
     out[1 + 2 * k] = (double)ctx->c.ev_used[k];
     out[2 + 2 * k] = ms;
+    out[5 + k] = covered;
+  }
+  return MQS_OK;
+}
+
+int mqs_profile_trace(mqs_ctx* ctx, int32_t kind, double* out, int32_t max_launches,
+                      int32_t* count) {
+  MQS_TRY(enter(ctx));
+  if (kind < 0 || kind > 1 || !count || (max_launches > 0 && !out)) {
+    set_error("bad arguments to mqs_profile_trace");
+    return MQS_EINVAL;
+  }
+  const Ctx& c = ctx->c;
+  *count = (int32_t)c.ev_used[kind];
+  if (!c.prof_t0) return MQS_OK;
+  MQS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  for (size_t j = 0; j < c.ev_used[kind] && (int64_t)j < max_launches; ++j) {
+    float a = 0.0f, z = 0.0f;
+    MQS_CUDA_TRY(cudaEventSynchronize(c.ev[kind][j].second));
+    MQS_CUDA_TRY(cudaEventElapsedTime(&a, c.prof_t0, c.ev[kind][j].first));
+    MQS_CUDA_TRY(cudaEventElapsedTime(&z, c.prof_t0, c.ev[kind][j].second));
+    out[2 * j] = a;
+    out[2 * j + 1] = z;
   }
   return MQS_OK;
 }

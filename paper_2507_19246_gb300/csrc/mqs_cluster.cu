@@ -106,6 +106,7 @@ struct CSmem {
   int sdone;                                 // rounds whose s is in the ring
   int pdone;                                 // rounds whose pre is in shared memory
   int err;                                   // a wait ran out
+  int flag_pub[2];                           // step-boundary snapshot: 1 error, 2 cancelled
   double red[kNW];
   double cred[CL][2];                        // per-rank partial sums for cluster reductions
 };
@@ -511,7 +512,10 @@ struct Subst {
           const int64_t r = rounds + g - 1;
           const uint32_t mb = smem_addr(&sm.mbar[r & 1]);
           mbar_wait(mb, (uint32_t)((r >> 1) & 1), &sm.err);
-          if (threadIdx.x == 0) mbar_arm(mb, kShareTx<CL>);   // round r + 2
+          // round r + 2; after an expired wait the phase may be incomplete and
+          // is not armed again
+          if (threadIdx.x == 0 && !*reinterpret_cast<volatile int*>(&sm.err))
+            mbar_arm(mb, kShareTx<CL>);
           const double* Vb = &sm.V[(g - 1) & 1][0][0];
           constexpr int NV = CL / S::LPR > 0 ? CL / S::LPR : 1;   // shares summed by this lane
           double v[NV];
@@ -554,10 +558,14 @@ struct Subst {
         } else {
           const uint32_t la = smem_addr(&sm.V[g & 1][q][x_r]);
           const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
+          // after an expired wait this CTA's values are invalid: it stops
+          // sending, so the other CTAs' waits run out too and the lane leaves
+          // at the next step boundary
+          const bool failed = *reinterpret_cast<volatile int*>(&sm.err) != 0;
           for (int p = x_g; p < CL; p += S::LPR) {
             if (p == q)
               sm.V[g & 1][q][x_r] = v;   // own share: ordered by the group barrier of the next round
-            else
+            else if (!failed)
               st_async(map_rank(la, p), v, map_rank(lm, p));
           }
         }
@@ -614,13 +622,52 @@ __device__ void cluster_finish(CSmem<CL>& sm, const DirectLane& D) {
   if (threadIdx.x == 0 && sm.err && D.status_out) atomicOr(D.status_out, MQS_ST_TIMEOUT);
 }
 
+// Flags of a step boundary, identical on every CTA of the cluster: each CTA
+// publishes its error flag (bit 0) and rank 0 the cancellation state (bit 1)
+// into slot `slot` before the barrier; after it every CTA ors the slots of all
+// ranks.  A slot is written again two boundaries later, after a barrier that
+// every CTA passes only once it has read the slot.
+// System-scope load of a word the host writes (host-mapped memory).
+__device__ __forceinline__ int32_t load_sys(const volatile int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int CL>
+__device__ int boundary_flags(CSmem<CL>& sm, const DirectConst& kc, unsigned q, int slot) {
+  if (threadIdx.x == 0) {
+    int f = *reinterpret_cast<volatile int*>(&sm.err) ? 1 : 0;
+    if (q == 0 && kc.stop && load_sys(kc.stop) < kc.iter) f |= 2;
+    sm.flag_pub[slot] = f;
+  }
+  int f = 0;
+  if constexpr (CL == 1) {
+    __syncthreads();
+    f = *reinterpret_cast<volatile int*>(&sm.flag_pub[slot]);
+  } else {
+    cluster_sync_all();
+    cg::cluster_group cl = cg::this_cluster();
+    for (int p = 0; p < CL; ++p) f |= *cl.map_shared_rank(&sm.flag_pub[slot], p);
+  }
+  return f;
+}
+
 // Advance one lane by n_steps steps.  a_init: initial state (all nodes
 // readable) or nullptr for zero; on return the final state is in D.a0 (own
 // nodes).  Returns this thread's share of the raw QoI sum when want_qoi.
+// `left` receives the step-boundary flags that ended the run early (1: a wait
+// ran out, 2: the launch was cancelled; 0: all steps ran), the same on every
+// CTA of the cluster.
 template <int CL>
 __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
                                     const double* a_init, int n_steps, int64_t k0, unsigned q,
-                                    Subst<CL>& sub, double* w, bool want_qoi) {
+                                    Subst<CL>& sub, double* w, bool want_qoi, int& left) {
+  left = 0;
+  if (kc.stop) {   // a launch queued behind the iteration that met the stopping rule
+    left = boundary_flags<CL>(sub.sm, kc, q, 1);
+    if (left) return 0.0;
+  }
   const int n = kc.n;
   const Own<CL> own{n, (int)q};
   const int n_own = own.count();
@@ -673,11 +720,10 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
       const int i = __ldg(kc.perm + pi);
       a1[i] = w[pi] * __ldg(D.invd + pi);                    // x = D^-1 u
     }
-    if constexpr (CL == 1) {                                  // a1 complete for y = M a1
-      __syncthreads();
-    } else {
-      cluster_sync_all();
-    }
+    // a1 complete for y = M a1; the whole cluster leaves here together after
+    // an expired wait or a cancellation
+    left = boundary_flags<CL>(sub.sm, kc, q, step & 1);
+    if (left) return qacc;
     for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
       const int pi = own.row(idx);
       if (pi >= n) continue;
@@ -718,8 +764,9 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
   cluster_setup<CL>(sm);
   Subst<CL> sub(D, w, sm, kc.n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
-  const double part = cluster_integrate<CL>(kc, D, D.init_from_a0 ? D.a0 : nullptr, D.n_steps,
-                                            D.k0, q, sub, w, true);
+  const double* init = D.init_from_a0 ? (D.a_init ? D.a_init : D.a0) : nullptr;
+  int left = 0;
+  const double part = cluster_integrate<CL>(kc, D, init, D.n_steps, D.k0, q, sub, w, true, left);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
   if (threadIdx.x == 0 && q == 0)
     D.qoi_out[0] = kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s;
@@ -743,10 +790,14 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   cluster_setup<CL>(sm);
   Subst<CL> sub(D, w, sm, n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
-  for (int s = ch.s_begin; s < ch.M - 1; ++s) {
+  const int s_stop = min(ch.s_end, ch.M - 1);
+  for (int s = ch.s_begin; s < s_stop; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
-    cluster_integrate<CL>(kc, D, ch.U + base, ch.steps_per_slice,
-                          (int64_t)s * ch.steps_per_slice, q, sub, w, false);
+    const double* U0 = s == ch.s_first ? ch.U_prev : ch.U_cur;
+    int left = 0;
+    cluster_integrate<CL>(kc, D, U0 + base, ch.steps_per_slice,
+                          (int64_t)s * ch.steps_per_slice, q, sub, w, false, left);
+    if (left) break;   // every CTA of the cluster leaves at the same slice
     double j2 = 0.0, u2 = 0.0;
     for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
       const int pi = own.row(idx);
@@ -754,10 +805,10 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
       const int i = __ldg(kc.perm + pi);
       const double gn = D.a0[i];
       const double un = ch.first_sweep ? gn : ch.E[base + i] + (gn - ch.G[base + i]);
-      const double du = un - ch.U[base + n + i];
+      const double du = un - ch.U_prev[base + n + i];
       j2 = fma(du, du, j2);
       u2 = fma(un, un, u2);
-      ch.U[base + n + i] = un;
+      ch.U_cur[base + n + i] = un;
       ch.G[base + i] = gn;
     }
     j2 = cluster_sum<CL>(cta_sum(j2, sm.red), sm, 0, q);
@@ -975,7 +1026,7 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
     }
     mbar_wait(smem_addr(&mb[par]), (uint32_t)((j >> 1) & 1), &err);
     __syncthreads();
-    if (threadIdx.x == 0) mbar_arm(smem_addr(&mb[par]), tx_of(j + 2));   // column j + 2
+    if (threadIdx.x == 0 && !err) mbar_arm(smem_addr(&mb[par]), tx_of(j + 2));   // column j + 2
     // rank-1 update of the own rows (j + 1, j + total], entries j + 1 .. i
     for (int k = warp; k < n_own; k += kNW) {
       const int i = first + NC * k;

@@ -571,6 +571,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_propagate(const Direct
                                                                  DirectConst kc) {
   __shared__ typename Integrator<NT, PREC>::Smem sm;
   const DirectLane D = lanes[blockIdx.x];
+  if (D.init_from_a0 && D.a_init) {   // start state held elsewhere: into a0 first
+    for (int i = threadIdx.x; i < kc.n; i += NT) D.a0[i] = D.a_init[i];
+    __syncthreads();
+  }
   DLaneOut out;
   Integrator<NT, PREC>::run(kc, D, D.n_steps, D.k0, sm, out);
   if (threadIdx.x == 0) D.qoi_out[0] = out.qoi;
@@ -586,9 +590,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_chain(const DirectLane
   const int n = kc.n;
   const int sample = D.sample;
   D.init_from_a0 = 1;
-  for (int s = ch.s_begin; s < ch.M - 1; ++s) {
+  const int s_stop = min(ch.s_end, ch.M - 1);
+  for (int s = ch.s_begin; s < s_stop; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
-    for (int i = threadIdx.x; i < n; i += NT) D.a0[i] = ch.U[base + i];
+    const double* U0 = s == ch.s_first ? ch.U_prev : ch.U_cur;
+    for (int i = threadIdx.x; i < n; i += NT) D.a0[i] = U0[base + i];
     __syncthreads();
     DLaneOut out;
     Integrator<NT, PREC>::run(kc, D, ch.steps_per_slice, (int64_t)s * ch.steps_per_slice, sm, out);
@@ -596,10 +602,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_chain(const DirectLane
     for (int i = threadIdx.x; i < n; i += NT) {
       const double gn = D.a0[i];
       const double un = ch.first_sweep ? gn : ch.E[base + i] + (gn - ch.G[base + i]);
-      const double du = un - ch.U[base + n + i];
+      const double du = un - ch.U_prev[base + n + i];
       j2 = fma(du, du, j2);
       u2 = fma(un, un, u2);
-      ch.U[base + n + i] = un;
+      ch.U_cur[base + n + i] = un;
       ch.G[base + i] = gn;
     }
     j2 = block_sum<NT>(j2, sm.red);

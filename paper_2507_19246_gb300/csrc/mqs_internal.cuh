@@ -84,9 +84,12 @@ struct MeshDev {
   DevBuf band_idx;               // [nnz] position of a lower-band entry in [n][bw+1], -1 above
 };
 
-// Reverse Cuthill-McKee ordering of a symmetric CSR pattern (host).
+// Reverse Cuthill-McKee ordering of a symmetric CSR pattern (host); boundary
+// ([n], or empty) marks the nodes next to the Dirichlet boundary, whose pieces
+// give a second candidate start set (the narrower band is kept).
 void rcm_order(int n, const std::vector<int32_t>& rowptr, const std::vector<int32_t>& colidx,
-               std::vector<int32_t>& perm, int32_t& bandwidth);
+               const std::vector<char>& boundary, std::vector<int32_t>& perm,
+               int32_t& bandwidth);
 
 // ---------------------------------------------------------------- solve lanes
 // One tile = L consecutive lanes that share a step size and a step count and
@@ -168,6 +171,7 @@ struct DirectLane {
   const float* invdf;
   const float* Binvf;
   const double* Av;        // FP64 A values of this lane's sample and dt (mixed residual)
+  const double* a_init;    // start state [n] when init_from_a0 (nullptr: start from a0 itself)
   double* b;               // FP64 right-hand side [n] (mixed)
   int32_t* status_out;     // MQS_ST_* bits of this lane (or-ed)
   double *a0, *a1, *y, *w; // lane vectors [n] (lane-major)
@@ -197,13 +201,25 @@ struct DirectConst {
   int32_t cluster;         // 0: one-CTA kernels of mqs_direct.cu; 1, 2, 4, 8: CTAs per lane
   int32_t stall_test;      // 1: the one-CTA cluster kernel's first wait is on a count
                            //    nothing reaches (tests the bounded wait and its status)
-  int32_t pad3_;
+  int32_t iter;            // Parareal iteration of this launch (cancellation check)
+  // Parareal cancellation (cluster kernels): a launch of iteration `iter`
+  // leaves its step loop at the first step boundary where *stop < iter; the
+  // word lives in host-mapped memory and is raised by the host once an earlier
+  // iteration met the stopping rule (nullptr: never cancelled)
+  const volatile int32_t* stop;
 };
 
+// One launch of the Parareal coarse sweep of iteration k over slices
+// [s_begin, min(s_end, M - 1)).  The sweep starts at slice s_first (k - 1, or
+// 0 for k = 0) from U_prev[s_first]; later slices start from U_cur, which it
+// writes: U_cur[s + 1] = E[s] + (G_new - G[s]) (Eq. 12), and the jump is
+// measured against U_prev[s + 1].  The non-pipelined driver passes one buffer
+// as both U_prev and U_cur.
 struct DirectChain {
-  double *U, *E, *G;       // [samples][M][n] slice starts, fine ends, previous coarse ends
-  int32_t M, s_begin, steps_per_slice, first_sweep;
-  double *jump2, *norm2;   // [samples][M]
+  double *U_prev, *U_cur;  // [samples][M][n] slice starts of iterations k-1 and k
+  double *E, *G;           // [samples][M][n] fine ends of iteration k, previous coarse ends
+  int32_t M, s_first, s_begin, s_end, steps_per_slice, first_sweep;
+  double *jump2, *norm2;   // [samples][M] of iteration k
 };
 
 // mqs_direct.cu
@@ -263,6 +279,8 @@ int transpose_to_rows(const double* lanes, int64_t xs, int n, int n_samples, int
                       int lane_offset, double* out, cudaStream_t st);
 int transpose_from_rows(const double* rows, int n, int n_samples, double* lanes, int64_t xs,
                         cudaStream_t st);
+int gather_parareal_qraw(const double* qraw2, int64_t lanes, int M, int K, double* out,
+                         cudaStream_t st);
 int finish_qoi(const double* raw_fine, const double* raw_coarse, int n_samples, int lanes_per_sample,
                double scale_fine, double scale_coarse, double* qoi, cudaStream_t st);
 int mlmc_accumulate_dev(const double* qoi, int n_samples, int level, double* record,

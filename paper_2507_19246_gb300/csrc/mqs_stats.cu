@@ -57,6 +57,19 @@ __global__ void k_finish_qoi(const double* __restrict__ rf, const double* __rest
   qoi[2 * (int64_t)s + 1] = rc ? rc[s] * sc : 0.0;
 }
 
+// Pipelined Parareal keeps the per-slice raw QoI partials of iteration k in
+// buffer k mod 2 ([2][lanes], lane = sample * M + slice).  Slice s last ran
+// its fine propagator in iteration min(K, s + 1): out[l] takes that buffer's
+// value.
+__global__ void k_gather_qraw(const double* __restrict__ q2, int64_t lanes, int M, int K,
+                              double* __restrict__ out) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= lanes) return;
+  const int s = (int)(l % M);
+  const int k = min(K, s + 1);
+  out[l] = q2[(int64_t)(k & 1) * lanes + l];
+}
+
 // Neumaier's compensated summation step.
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   const double t = s + x;
@@ -158,6 +171,14 @@ int transpose_from_rows(const double* rows, int n, int ns, double* lanes, int64_
 int finish_qoi(const double* rf, const double* rc, int ns, int lps, double sf, double sc,
                double* qoi, cudaStream_t st) {
   k_finish_qoi<<<grid_of(ns, 128), 128, 0, st>>>(rf, rc, ns, lps, sf, sc, qoi);
+  MQS_CUDA_TRY(cudaGetLastError());
+  count_launch();
+  return MQS_OK;
+}
+
+int gather_parareal_qraw(const double* q2, int64_t lanes, int M, int K, double* out,
+                         cudaStream_t st) {
+  k_gather_qraw<<<grid_of(lanes, 128), 128, 0, st>>>(q2, lanes, M, K, out);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

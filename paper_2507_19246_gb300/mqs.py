@@ -14,6 +14,14 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+# The banded Parareal driver keeps up to 16 fine chunks in flight on streams
+# of their own.  CUDA multiplexes streams onto CUDA_DEVICE_MAX_CONNECTIONS
+# hardware queues (8 unless set), and streams that share a queue serialise
+# behind each other's event waits.  The setting is read when CUDA initialises
+# in the process, so it only takes effect if nothing has initialised CUDA yet;
+# an explicit setting by the caller is kept.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np
 
 from . import build as _build
@@ -52,6 +60,8 @@ _SIGS = {
     "mqs_mlmc_readout": (C.c_int, [_P, _P, C.POINTER(_f64), C.POINTER(_f64)]),
     "mqs_profile": (C.c_int, [_P, _i32]),
     "mqs_profile_read": (C.c_int, [_P, _P]),
+    "mqs_profile_trace": (C.c_int, [_P, _i32, _P, _i32, C.POINTER(_i32)]),
+    "mqs_measure_peak": (C.c_int, [_i32, _P, _i32, C.POINTER(_f64)]),
     "mqs_propagate_noalloc": (C.c_int, [_i32, _P, _i32, _P, _P, _i64, _i32, _P, _P, _P, _P, _i32,
                                         _P, _P, _P, _f64, _f64, _i32, _f64, _i32, _f64, _i32, _P,
                                         _P, _P]),
@@ -231,9 +241,23 @@ def mqs_profile(ctx, enable):
 
 
 def mqs_profile_read(ctx):
-    out = np.zeros(5)
+    out = np.zeros(7)
     _check("mqs_profile_read", load().mqs_profile_read(ctx, _ptr(out)))
     return out
+
+
+def mqs_profile_trace(ctx, kind, max_launches=100000):
+    out = np.zeros(2 * max_launches)
+    cnt = _i32()
+    _check("mqs_profile_trace", load().mqs_profile_trace(ctx, kind, _ptr(out), max_launches,
+                                                         C.byref(cnt)))
+    return out[:2 * min(cnt.value, max_launches)].reshape(-1, 2)
+
+
+def mqs_measure_peak(device, stream, precision):
+    out = _f64()
+    _check("mqs_measure_peak", load().mqs_measure_peak(device, stream, precision, C.byref(out)))
+    return out.value
 
 
 def mqs_propagate_noalloc(device, stream, n, rowptr, colidx, nnz, n_lanes, A, M, K, Dinv,
@@ -348,11 +372,16 @@ class Context:
         mqs_profile(self.h, enable)
 
     def profile_read(self):
-        """[launches, step-kernel launches, ms, sweep-kernel launches, ms]"""
+        """[launches, step-kernel launches, ms, sweep-kernel launches, ms,
+        step-kernel covered ms, sweep-kernel covered ms]"""
         return mqs_profile_read(self.h)
 
     def set_test_hook(self, hook):
         mqs_set_test_hook(self.h, hook)
+
+    def profile_trace(self, kind):
+        """[launches][2]: start and end (ms) of each recorded launch of a kind."""
+        return mqs_profile_trace(self.h, kind)
 
     def free_batch(self, batch):
         mqs_free_batch(self.h, batch)

@@ -3,6 +3,10 @@ import sys
 
 import pytest
 
+# before anything initialises CUDA: hardware queues for the pipelined Parareal
+# streams (see paper_2507_19246_gb300/mqs.py)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

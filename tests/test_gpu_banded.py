@@ -437,3 +437,63 @@ def test_banded_default_shapes_many_lanes(ctx, mqs, n_samples):
         qc, acc, _ = stepper.solve_sample(mesh, p[s], dt0, 4, stepper.QOI_JOULE)
         assert abs(q[s, 0] - qf) <= TOL * abs(qf) and abs(q[s, 1] - qc) <= TOL * abs(qc), s
         assert _rel(a[s], af) <= TOL and _rel(ac[s], acc) <= TOL, s
+
+
+@pytest.mark.parametrize("M,cf,n_samples", [(16, 4, 1), (64, 1, 2), (8, 2, 3)])
+def test_pipelined_parareal_is_bitwise_the_stepwise_driver(ctx, mqs, monkeypatch, M, cf,
+                                                           n_samples):
+    """Parareal with the coarse sweep overlapped by the next iteration's fine
+    chunks (and that iteration cancelled once the stopping rule holds) runs
+    the same per-lane arithmetic as the driver that finishes each iteration
+    before the next: same K, bitwise the same QoI and final states; and both
+    match the oracle's Parareal.  Chunks of 1 and of 4 slices, several samples."""
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(n_samples, 0, seed=50 + M)
+    n_steps, tol = 256, 1e-8
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    out = []
+    for pipe in ("1", "0"):
+        monkeypatch.setenv("MQS_PARAREAL_PIPELINE", pipe)
+        b = ctx.set_samples(mid, p)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+        K = ctx.propagate(b, 0, dt, n_slices=M, coarse_factor=cf, max_par_iters=M, par_tol=tol)
+        q, st = ctx.read_qoi(b)
+        assert not st.any()
+        out.append((K, q.copy(), ctx.read_state(b, 0), ctx.read_stats(b)))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[0][3], out[1][3])      # the same executed-step counts
+    K, q, a = out[0][0], out[0][1], out[0][2]
+    for s in range(n_samples):
+        d = fem.Discretisation(mesh, p[s])
+        ref = parareal.parareal_sample(d, dt, n_steps, M, cf, 0.0, stepper.QOI_JOULE,
+                                       max_iter=K)
+        q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
+        assert abs(q[s, 0] - q_ref) <= TOL * abs(q_ref), s
+        assert _rel(a[s], ref["a_end"]) <= TOL, s
+
+
+def test_pipelined_parareal_iteration_limit(ctx, mqs):
+    """max_par_iters below the slice count: the last allowed iteration ends the
+    run without a speculative one; K and the QoI match the oracle's Parareal
+    stopped at that iteration."""
+    mesh = meshes.annulus("5k")
+    p = params.annulus_nominal(1)
+    n_steps, M, cf = 128, 16, 2
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    for kmax in (1, 2):
+        b = ctx.set_samples(mid, p)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+        K = ctx.propagate(b, 0, dt, n_slices=M, coarse_factor=cf, max_par_iters=kmax,
+                          par_tol=0.0)
+        q, st = ctx.read_qoi(b)
+        assert K == kmax and not st.any()
+        ref = parareal.parareal_sample(fem.Discretisation(mesh, p[0]), dt, n_steps, M, cf, 0.0,
+                                       stepper.QOI_JOULE, max_iter=kmax)
+        q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
+        assert abs(q[0, 0] - q_ref) <= TOL * abs(q_ref)
+        assert _rel(ctx.read_state(b, 0)[0], ref["a_end"]) <= TOL

@@ -25,8 +25,8 @@ def reference():
     return wl, ref
 
 
-@pytest.mark.parametrize("solver", ["banded", "pcg"])
-def test_parareal_annulus20k_full_size(reference, solver):
+@pytest.mark.parametrize("solver", ["banded", "banded-stepwise", "pcg"])
+def test_parareal_annulus20k_full_size(reference, solver, monkeypatch):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.fail("GPU test needs a CUDA device")
@@ -34,10 +34,13 @@ def test_parareal_annulus20k_full_size(reference, solver):
 
     wl, ref = reference
     mesh, p = wl["mesh"], wl["params"]
+    # "banded": the bench's path (sweep and fine chunks overlapped);
+    # "banded-stepwise": each Parareal iteration finished before the next
+    monkeypatch.setenv("MQS_PARAREAL_PIPELINE", "0" if solver == "banded-stepwise" else "1")
     with mqs.Context(0) as ctx:
         mid = ctx.upload_mesh(mesh)
         b = ctx.set_samples(mid, p)
-        if solver == "banded":
+        if solver.startswith("banded"):
             ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
         ctx.set_time(b, 0.0, wl["t_end"], 50.0, wl["qoi"])
         K = ctx.propagate(b, 0, wl["dt"], n_slices=wl["n_slices"], coarse_factor=wl["cf"],
@@ -46,6 +49,12 @@ def test_parareal_annulus20k_full_size(reference, solver):
                           cg_max_iters=20000 if solver == "pcg" else 1)
         q, st = ctx.read_qoi(b)
         a = ctx.read_state(b, 0)
+    if solver.startswith("banded"):
+        ref.setdefault("banded_runs", {})[solver] = (q.copy(), a.copy())
+        runs = ref["banded_runs"]
+        if len(runs) == 2:   # the overlapped driver is bitwise the stepwise one
+            (q1, a1), (q2, a2) = runs.values()
+            assert np.array_equal(q1, q2) and np.array_equal(a1, a2)
     assert not st.any()
     assert K == ref["iters"]
     assert abs(q[0, 0] - ref["q"]) <= 1e-10 * abs(ref["q"]), (q[0, 0], ref["q"])
