@@ -270,6 +270,14 @@ int mqs_propagate_noalloc(int32_t device, void* cuda_stream, int32_t n, const in
                           double freq_hz, int32_t qoi_kind, double cg_tol, int32_t cg_max_iters,
                           double* a_out, double* qoi_out, int32_t* status_out);
 
+/* Lane slots: how many independent sample solves ("lanes") the banded
+ * stepping keeps resident on the GPU at once in its throughput form (one
+ * 256-thread CTA per lane, several per SM).  These are the "cores" n_c of the
+ * paper's batching model (Sec. II-D, Eq. 24-25): a level with N samples runs
+ * in about N (1 + C_{l-1}/C_l) / slots batches, and the finest level can give
+ * each sample floor(slots / (N_L (1 + C_{L-1}/C_L))) lanes for Parareal slices. */
+int mqs_lane_slots(mqs_ctx* ctx, int32_t precision, int32_t* slots);
+
 /* Test hook, for tests of the failure path only (0 = off, the default).
  * MQS_TEST_HOOK_STALL: on this context, the first wait of every banded
  * stepping lane that runs as one CTA per lane (cluster kernels with one CTA)

@@ -1903,6 +1903,18 @@ int mqs_mlmc_readout(mqs_ctx* ctx, double* levels, double* estimate, double* rms
   return MQS_OK;
 }
 
+int mqs_lane_slots(mqs_ctx* ctx, int32_t precision, int32_t* slots) {
+  MQS_TRY(enter(ctx));
+  if (!slots || (precision != MQS_FP64 && precision != MQS_MIXED)) {
+    set_error("bad arguments to mqs_lane_slots");
+    return MQS_EINVAL;
+  }
+  const int r = direct_lane_slots(precision == MQS_MIXED ? 1 : 0);
+  if (r < 0) return MQS_ECUDA;
+  *slots = r;
+  return MQS_OK;
+}
+
 int mqs_set_test_hook(mqs_ctx* ctx, int32_t hook) {
   MQS_TRY(enter(ctx));
   if (hook != 0 && hook != MQS_TEST_HOOK_STALL) {

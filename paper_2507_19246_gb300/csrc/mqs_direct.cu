@@ -716,6 +716,22 @@ int launch_chain_t(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc
   return MQS_OK;
 }
 
+// Lanes the throughput form (256 threads per lane, work vector in L2) keeps
+// resident on the whole GPU at once: its CTAs per SM times the SM count.
+int direct_lane_slots(int mixed) {
+  int dev = 0, n_sm = 0, per_sm = 0;
+  MQS_CUDA_TRY(cudaGetDevice(&dev));
+  MQS_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const cudaError_t e = mixed
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_direct_propagate<256, 1>, 256, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_direct_propagate<256, 0>, 256, 0);
+  if (e != cudaSuccess) {
+    set_error("occupancy query failed: %s", cudaGetErrorString(e));
+    return -1;
+  }
+  return per_sm * n_sm;
+}
+
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
   if (kc.mixed)

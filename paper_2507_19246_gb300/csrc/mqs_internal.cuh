@@ -229,6 +229,7 @@ int band_factor(const MeshDev& m, const double* A, int64_t vs, int n_fac, T* LB,
 int block_count(int n);
 int launch_direct(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
 int direct_smem_max_n(int mixed);
+int direct_lane_slots(int mixed);   // -1 on error (message set)
 int launch_direct_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                         const DirectChain& ch, cudaStream_t st);
 

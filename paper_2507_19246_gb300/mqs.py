@@ -66,6 +66,7 @@ _SIGS = {
                                         _P, _P, _P, _f64, _f64, _i32, _f64, _i32, _f64, _i32, _P,
                                         _P, _P]),
     "mqs_set_test_hook": (C.c_int, [_P, _i32]),
+    "mqs_lane_slots": (C.c_int, [_P, _i32, C.POINTER(_i32)]),
     "mqs_free_batch": (C.c_int, [_P, _i32]),
     "mqs_free_mesh": (C.c_int, [_P, _i32]),
 }
@@ -271,6 +272,12 @@ def mqs_propagate_noalloc(device, stream, n, rowptr, colidx, nnz, n_lanes, A, M,
         qoi_kind, cg_tol, cg_max_iters, _ptr(a_out), _ptr(qoi_out), _ptr(status_out)))
 
 
+def mqs_lane_slots(ctx, precision=MQS_FP64) -> int:
+    out = _i32()
+    _check("mqs_lane_slots", load().mqs_lane_slots(ctx, precision, C.byref(out)))
+    return out.value
+
+
 def mqs_set_test_hook(ctx, hook):
     _check("mqs_set_test_hook", load().mqs_set_test_hook(ctx, int(hook)))
 
@@ -375,6 +382,9 @@ class Context:
         """[launches, step-kernel launches, ms, sweep-kernel launches, ms,
         step-kernel covered ms, sweep-kernel covered ms]"""
         return mqs_profile_read(self.h)
+
+    def lane_slots(self, precision=MQS_FP64):
+        return mqs_lane_slots(self.h, precision)
 
     def set_test_hook(self, hook):
         mqs_set_test_hook(self.h, hook)

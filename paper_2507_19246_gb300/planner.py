@@ -12,7 +12,11 @@ Host-side planning around the GPU path (Sec. II-B to II-D):
   Eq. 25, and the finite-core speedup s_nc.
 * ``run_adaptive_mlmc`` -- levels treated sequentially as the paper
   prescribes: pilot samples estimate V_l, Eq. 11 sizes each level, the
-  remaining samples run, and the estimator of Eq. 9 is read out.
+  remaining samples run, and the estimator of Eq. 9 is read out; with
+  parareal=True the finest level runs Parareal on as many slices as Eq. 25
+  gives each of its samples from the GPU's lane slots.
+* ``figure_curves`` -- the speedup and effort curves of Fig. 1-2 from the
+  model (finite cores, one curve per iteration count).
 
 On one GPU the "cores" of the model are the lane slots the library runs at
 once; the model is unit-free, so costs may be seconds or solve-steps.
@@ -126,33 +130,95 @@ def finite_core_speedup(N, r, K, n_cores):
     return num / den
 
 
+def finite_core_effort_ratio(N, r, K, n_cores):
+    """Effort increase of the combined method with n_cores cores (the model
+    behind Fig. 2): the finest level's N_L samples each run Parareal on
+    n_c,para = Eq. 25 slices with fine cost C_L and coarse cost C_{L-2}
+    (Eq. 16 with M = n_c,para), the other levels as in plain MLMC; divided by
+    the plain MLMC effort sum_l N_l C_l.  Costs in units of C_0 (Eq. 20)."""
+    L = len(N) - 1
+    C = exponential_costs(1.0, r, L)
+    m = parareal_cores(n_cores, N[L], C[L], C[L - 1])
+    e_para = parareal_effort(K, m, C[L], C[L - 2])
+    return combined_effort(N, C, e_para) / mlmc_effort(N, C)
+
+
+def figure_curves(N, r, K_values, core_counts):
+    """Speedup (Fig. 1) and effort increase (Fig. 2) of the combined method
+    against the number of cores, one curve per iteration count K: returns
+    {K: (s_nc list, effort-ratio list)} over core_counts (counts that leave
+    fewer than two cores per finest-level sample are skipped: None)."""
+    L = len(N) - 1
+    C = exponential_costs(1.0, r, L)
+    out = {}
+    for K in K_values:
+        s, e = [], []
+        for nc in core_counts:
+            m = parareal_cores(nc, N[L], C[L], C[L - 1])
+            ok = m >= max(2, K)
+            s.append(finite_core_speedup(N, r, K, nc) if ok else None)
+            e.append(finite_core_effort_ratio(N, r, K, nc) if ok else None)
+        out[K] = (s, e)
+    return out
+
+
+def plan_finest_level(N_L, C_L, C_prev, slots, n_steps, coarse_factor, max_slices=64):
+    """Parareal on the finest level (Sec. II-D): Eq. 25 gives the lane slots
+    per sample, n = floor(slots / (N_L (1 + C_{L-1}/C_L))).  The slice count
+    is the largest power of two M <= min(n, max_slices) whose slices hold a
+    whole number of coarse steps (n_steps divisible by M * coarse_factor).
+    Returns (n, M); M = 1 means the level runs sequentially."""
+    n = parareal_cores(slots, N_L, C_L, C_prev) if N_L > 0 else 0
+    M = 1
+    while 2 * M <= min(n, max_slices) and n_steps % (2 * M * coarse_factor) == 0:
+        M *= 2
+    return n, (M if M >= 2 else 1)
+
+
 # ---------------------------------------------------------------- adaptive MLMC
 def run_adaptive_mlmc(ctx, mesh_id, sampler, dts, t_end, rmse_target, n_pilot=16,
-                      qoi_kind=1, solver=None, chunk=1024, max_per_level=1 << 20, **prop):
+                      qoi_kind=1, solver=None, chunk=1024, max_per_level=1 << 20,
+                      parareal=False, par_tol=1e-8, lane_slots=None, plan_out=None, **prop):
     """Sequential-level MLMC with run-time variance estimates (Sec. II-B).
 
     sampler(level, first, n) -> [n, n_params] parameters of samples
     first..first+n-1 of `level`; dts[l] the step of level l.  Each level first
     runs n_pilot samples, Eq. 11 (with the pilot variances of the levels run
     so far and C_l proportional to the step count) sets its size, and the
-    remaining samples run.  Returns (estimate, rmse, N_l, levels [N, mean,
-    var]).  All solves run through the library's C ABI.
+    remaining samples run.
+
+    parareal=True applies the combined method of Sec. II-D: once the finest
+    level L >= 2 is sized, plan_finest_level decides from the library's lane
+    slots (mqs_lane_slots, the "cores" of Eq. 24-25, or `lane_slots`) how many
+    slices each of its remaining samples gets; with two or more they run
+    Parareal (coarse propagator = level L-2, tolerance par_tol), else
+    sequentially.  plan_out (a dict) receives the decision: slots, n_c,para,
+    slices, the coarse factor and the Parareal iterations of each batch.
+
+    Returns (estimate, rmse, N_l, levels [N, mean, var]).  All solves run
+    through the library's C ABI.
     """
-    from . import mqs
     L = len(dts)
     steps = [round(t_end / dt) for dt in dts]
     cost = [steps[l] + (steps[l - 1] if l else 0) for l in range(L)]
     ctx.mlmc_reset(L)
     done = [0] * L
+    plan = {"slices": 1, "iters": []}
 
-    def run(level, first, n):
+    def run(level, first, n, slices=1, cf=1):
         for s0 in range(first, first + n, chunk):
             m = min(chunk, first + n - s0)
             b = ctx.set_samples(mesh_id, sampler(level, s0, m))
             if solver is not None:
                 ctx.set_solver(b, solver)
             ctx.set_time(b, 0.0, t_end, 50.0, qoi_kind)
-            ctx.propagate(b, level, dts[level], dt_prev=dts[level - 1] if level else 0.0, **prop)
+            if slices > 1:
+                k = ctx.propagate(b, level, dts[level], dt_prev=dts[level - 1] if level else 0.0,
+                                  n_slices=slices, coarse_factor=cf, max_par_iters=slices,
+                                  par_tol=par_tol, **prop)
+                plan["iters"].append((s0, m, k))
+            else:
+                ctx.propagate(b, level, dts[level], dt_prev=dts[level - 1] if level else 0.0, **prop)
             ctx.mlmc_accumulate(b, level)
             ctx.free_batch(b)
 
@@ -165,8 +231,19 @@ def run_adaptive_mlmc(ctx, mesh_id, sampler, dts, t_end, rmse_target, n_pilot=16
         # size the levels seen so far; only this level can still grow
         N = allocate_samples(variances, cost[:l + 1], rmse_target, n_min=n_pilot)
         target = int(min(max(N[l], n_pilot), max_per_level))
+        slices, cf = 1, 1
+        if parareal and l == L - 1 and L >= 3 and target > done[l]:
+            slots = lane_slots if lane_slots is not None else ctx.lane_slots(
+                prop.get("precision", 0))
+            cf = int(round(dts[l - 2] / dts[l]))
+            n_para, slices = plan_finest_level(target - done[l], steps[l], steps[l - 1], slots,
+                                               steps[l], cf)
+            plan.update(slots=slots, n_c_para=n_para, slices=slices, coarse_factor=cf,
+                        first_parareal_sample=done[l])
         if target > done[l]:
-            run(l, done[l], target - done[l])
+            run(l, done[l], target - done[l], slices, cf)
             done[l] = target
+    if plan_out is not None:
+        plan_out.update(plan)
     lv, est, rmse = ctx.mlmc_readout()
     return est, rmse, list(done), lv

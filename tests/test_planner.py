@@ -52,3 +52,42 @@ def test_allocation_meets_the_target_and_follows_eq11():
     # halving eps quadruples the samples
     N2 = P.allocate_samples(V, C, eps / 2)
     assert np.all(N2 >= 4 * N - 4)
+
+
+def test_figure_curves_tend_to_the_unlimited_core_limits():
+    """Fig. 1-2 of Sec. II-D from the model (r = 10, L = 2, V_l ~ 10^-2l, N_l
+    by Eq. 11).  With unlimited cores every level is one batch and the
+    Parareal time K/M (r^L + (M - (K+1)/2) r^{L-2}) tends to K r^{L-2}; with
+    K = r that is C_{L-1} and the speedup tends to Eq. 21's bound.  The effort
+    ratio tends to (sum_{l<L} N_l C_l + N_L K (C_L + C_{L-2})) / sum N_l C_l
+    (Eq. 16 with M -> infinity)."""
+    r, L = 10, 2
+    V = [10.0 ** (-2 * l) for l in range(L + 1)]
+    C = P.exponential_costs(1.0, r, L)
+    N = [int(n) for n in P.allocate_samples(V, C, 1e-2)]
+    big = 10 ** 12
+    curves = P.figure_curves(N, r, [1, 2, r], [180, 10 ** 4, big])
+    s_big = curves[r][0][-1]
+    assert s_big == pytest.approx(P.speedup_bound(r, L), rel=1e-6)
+    for K in (1, 2, r):
+        eps_lim = (sum(n * c for n, c in zip(N[:-1], C[:-1])) + N[-1] * K * (C[L] + C[L - 2])) \
+            / sum(n * c for n, c in zip(N, C))
+        assert curves[K][1][-1] == pytest.approx(eps_lim, rel=1e-6)
+        # more iterations cost more effort at every core count
+    for i in range(3):
+        e = [curves[K][1][i] for K in (1, 2, r) if curves[K][1][i] is not None]
+        assert e == sorted(e)
+    # too few cores for two slices per finest-level sample: no point on the curve
+    tiny = P.figure_curves(N, r, [2], [N[-1]])
+    assert tiny[2] == ([None], [None])
+
+
+def test_plan_finest_level_follows_eq25():
+    # 608 lane slots, 8 finest samples, C_{L-1}/C_L = 1/2: floor(608 / 12) = 50
+    # slots each; 128 steps with coarse factor 4 allow 32 slices of one coarse step
+    assert P.plan_finest_level(8, 128.0, 64.0, 608, 128, 4) == (50, 32)
+    # many samples: fewer than two slots each -> sequential
+    assert P.plan_finest_level(500, 128.0, 64.0, 608, 128, 4) == (0, 1)
+    # the slice count must divide the steps in whole coarse steps
+    assert P.plan_finest_level(2, 128.0, 64.0, 608, 96, 4) == (202, 8)
+    assert P.plan_finest_level(2, 128.0, 64.0, 608, 4096, 64, max_slices=64) == (202, 64)
