@@ -557,6 +557,9 @@ def run_ours(args, wl, rank, world, dist):
     # ---- MLMC time-to-RMSE (configs' MLMC workload), FP64 and mixed
     if not args.no_extras and wl["name"] == "parareal_annulus20k":
         line["mlmc"] = mlmc_records(args, ctx, mqs, torch, stream)
+    # ---- the request server under a Poisson stream (p50/p99 latency)
+    if not args.no_extras and wl["name"] == "parareal_annulus20k":
+        line["serving"] = serving_record(ctx, mqs)
     # ---- CPU baseline: the oracle on the host cores (after the GPU work)
     if not args.no_cpu_baseline and wl["n_slices"] > 1:
         pool = oracle_parareal_pool(wl)
@@ -658,6 +661,70 @@ def mlmc_records(args, ctx, mqs, torch, stream):
     out["mixed_over_fp64_throughput"] = (out["mixed"]["sample_dof_steps_per_s"] /
                                          out["fp64"]["sample_dof_steps_per_s"])
     return out
+
+
+def serving_record(ctx, mqs, n_requests=240, rate=40.0, seed=20250725, n_streams=32):
+    """The request server under a Poisson stream (the configs' serving
+    workload, scaled so that the run takes seconds): level samples (levels
+    0-2 with their level-(l-1) companions) and Parareal slices, on the 5k,
+    20k and 80k annuli with 256 or 1024 steps, submitted at their arrival
+    times; per-request latency from submission to completion."""
+    import numpy as np
+
+    from workloads import configs, meshes, params
+    rng = np.random.default_rng(seed)
+    names = ["5k", "20k", "80k"]
+    mids = {nm: ctx.upload_mesh(meshes.annulus(nm)) for nm in names}
+    nfree = {nm: ctx.mesh_info(mids[nm])[0] for nm in names}
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    reqs = []
+    for j in range(n_requests):
+        nm = rng.choice(names, p=[0.5, 0.4, 0.1])
+        steps = int(rng.choice([256, 1024]))
+        prow = params.annulus_samples(1, 3, seed=seed, first=j)[0]
+        if rng.random() < 0.7:
+            l = int(rng.integers(0, 3))
+            lanes = [(configs.level_dt(l), steps)]
+            if l:
+                lanes.append((configs.level_dt(l - 1), steps // 2))
+            reqs.append((nm, prow, mqs.MQS_REQ_LEVEL, lanes, 0))
+        else:
+            k0 = int(rng.integers(0, 4)) * steps
+            reqs.append((nm, prow, mqs.MQS_REQ_SLICE, [(configs.level_dt(2), steps)], k0))
+    units = sum(nfree[r[0]] * sum(n for _, n in r[3]) for r in reqs)
+    lat, done = [], {}
+    with mqs.Server(ctx, n_streams=n_streams, max_batch_lanes=608) as srv:
+        t0 = time.perf_counter()
+        nxt, peak_inflight, peak_queue = 0, 0, 0
+        ids = {}
+        while len(done) < n_requests:
+            now = time.perf_counter() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                nm, prow, kind, lanes, k0 = reqs[nxt]
+                (dt, n), prev = lanes[0], (lanes[1] if len(lanes) > 1 else (0.0, 0))
+                rid = srv.submit(mids[nm], prow, kind, mqs.MQS_QOI_JOULE, 0.0, dt, n,
+                                 dt_prev=prev[0], n_steps_prev=prev[1], k0=k0)
+                ids[rid] = nxt
+                nxt += 1
+            inf, q = srv.progress()
+            peak_inflight, peak_queue = max(peak_inflight, inf), max(peak_queue, q)
+            for rid, qq, st, tm in zip(*srv.poll()):
+                done[int(rid)] = (tm[2] - tm[0], tm[1] - tm[0], int(st), tm[2])
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+    lat = np.array([v[0] for v in done.values()])
+    wait = np.array([v[1] for v in done.values()])
+    last_done = max(v[3] for v in done.values())
+    return {"requests": n_requests, "rate_per_s": rate, "streams": n_streams,
+            "mix": "70% level samples (levels 0-2, companions for l > 0), 30% Parareal slices; "
+                   "meshes 5k/20k/80k with p = 0.5/0.4/0.1; 256 or 1024 steps",
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "queue_wait_p50_s": float(np.percentile(wait, 50)),
+            "queue_wait_p99_s": float(np.percentile(wait, 99)),
+            "sample_dof_steps_per_s": units / last_done, "wall_s": wall,
+            "peak_in_flight": peak_inflight, "peak_queued": peak_queue,
+            "failed": int(sum(1 for v in done.values() if v[2]))}
 
 
 def run_mlmc(args, wl):

@@ -287,6 +287,66 @@ int mqs_lane_slots(mqs_ctx* ctx, int32_t precision, int32_t* slots);
 #define MQS_TEST_HOOK_STALL 1
 int mqs_set_test_hook(mqs_ctx* ctx, int32_t hook);
 
+/* ---------------------------------------------------------------- serving
+ * A request server on a context: continuous batching of independent sample
+ * solves of different meshes and step counts (the MLMC samples of Sec. II-B
+ * and the Parareal slices of Sec. II-C as separate requests).
+ *
+ * Requests wait in arrival order.  mqs_server_progress admits them, in that
+ * order, while their device footprint (per-sample values, a band Cholesky
+ * factor per step size, lane vectors) fits the HBM budget, as one batch per
+ * free stream; batches on different streams run at the same time, so a
+ * request admitted while others run starts as soon as SMs free up.  Every
+ * lane finishes on its own and reports through host-mapped memory, so a
+ * request completes when its own solves have, whatever its batch still does.
+ * All lanes use one launch shape (a 256-thread CTA each, work vector in L2),
+ * so a request's result does not depend on the other requests it ran with.
+ * Solves are FP64 with the banded direct solver (Eq. 7).  The server holds
+ * the context's meshes by id: do not free a mesh while its requests live.
+ * Single-threaded: call the server functions from one thread. */
+typedef struct mqs_server mqs_server;
+
+#define MQS_REQ_LEVEL 0   /* MLMC level sample: the level solve (dt, n_steps) from a(t0) = 0
+                             and, if dt_prev > 0, the level-(l-1) solve (dt_prev, n_steps_prev)
+                             on the same parameters; qoi = finished Q_l, Q_{l-1} (Eq. 9, 26) */
+#define MQS_REQ_SLICE 1   /* Parareal slice: n_steps fine steps (dt) from global step k0,
+                             starting from a_init (or zero); qoi[0] = the slice's raw QoI
+                             sum (what Parareal adds over slices), final state into a_out */
+
+/* hbm_budget: bytes of device memory admitted requests may hold (<= 0: 80%
+ * of the free memory at creation); n_streams: batches in flight (1..32);
+ * max_batch_lanes: lanes per batch (a level sample with a companion solve has
+ * two); freq_hz: supply frequency f of the source (Eq. 5). */
+int mqs_server_create(mqs_ctx* ctx, int64_t hbm_budget, int32_t n_streams,
+                      int32_t max_batch_lanes, double freq_hz, mqs_server** out);
+int mqs_server_destroy(mqs_server* srv);
+
+/* Queue one request; *request_id receives its id.  params: host,
+ * [n_params] in the layout of mqs_set_samples (copied).  a_init: host [n_free]
+ * (copied) or NULL; a_out: device [n_free] (caller-owned, written before the
+ * request completes) or NULL; both only for MQS_REQ_SLICE.  MQS_EINVAL for bad
+ * arguments or a footprint larger than the whole budget. */
+int mqs_server_submit(mqs_server* srv, int32_t mesh_id, int32_t n_params, const double* params,
+                      int32_t kind, int32_t qoi_kind, double t0, double dt, int32_t n_steps,
+                      double dt_prev, int32_t n_steps_prev, int64_t k0, const double* a_init,
+                      double* a_out, int64_t* request_id);
+
+/* Device bytes a request with `lanes` solves (1, or 2 for a level sample with
+ * its companion) on mesh_id holds while admitted. */
+int mqs_server_footprint(mqs_server* srv, int32_t mesh_id, int32_t qoi_kind, int32_t lanes,
+                         int64_t* bytes);
+
+/* Non-blocking scheduler pass (retire, release, admit, launch); *in_flight and
+ * *queued (may be NULL) receive the request counts afterwards. */
+int mqs_server_progress(mqs_server* srv, int32_t* in_flight, int32_t* queued);
+
+/* Up to max completed requests since the last call, in completion order:
+ * ids[c], qoi[c][2], status[c] (MQS_ST_* bits, may be NULL), times[c][3] =
+ * submit, admit and completion time (s, host clock from server creation; may
+ * be NULL); *count receives how many. */
+int mqs_server_poll(mqs_server* srv, int32_t max, int64_t* ids, double* qoi, int32_t* status,
+                    double* times, int32_t* count);
+
 /* Release a batch or a mesh (a mesh must have no live batch). */
 int mqs_free_batch(mqs_ctx* ctx, int32_t batch_id);
 int mqs_free_mesh(mqs_ctx* ctx, int32_t mesh_id);

@@ -278,6 +278,15 @@ struct mqs_ctx {
 
 using namespace mqs;
 
+namespace mqs {
+// Accessors for other translation units of the library (the request server).
+const MeshDev* ctx_mesh(mqs_ctx* ctx, int id) {
+  if (!ctx || id < 0 || id >= (int)ctx->c.meshes.size() || !ctx->c.meshes[id]) return nullptr;
+  return ctx->c.meshes[id].get();
+}
+int ctx_device(mqs_ctx* ctx) { return ctx->c.device; }
+}  // namespace mqs
+
 namespace {
 
 int enter(mqs_ctx* ctx) {
@@ -781,6 +790,7 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   d.w = w;
   d.qoi_out = qoi_out;
   d.vcol = sample;
+  d.qoi_scale = 1.0;
   const int R = m.n_regions, P = m.n_phases;
   const double* p = b.hparams.data() + (size_t)sample * b.n_params;
   for (int q = 0; q < kMaxPhases; ++q) {

@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
   const double part = cluster_integrate<CL>(kc, D, init, D.n_steps, D.k0, q, sub, w, true, left);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
   if (threadIdx.x == 0 && q == 0)
-    D.qoi_out[0] = kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s;
+    D.qoi_out[0] = (kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s) * D.qoi_scale;
   cluster_finish<CL>(sm, D);
 }
 

@@ -577,7 +577,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_direct_propagate(const Direct
   }
   DLaneOut out;
   Integrator<NT, PREC>::run(kc, D, D.n_steps, D.k0, sm, out);
-  if (threadIdx.x == 0) D.qoi_out[0] = out.qoi;
+  if (threadIdx.x == 0) D.qoi_out[0] = out.qoi * D.qoi_scale;
+  if (D.done_flag) {   // results (state, QoI, status) visible before the flag
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(D.done_flag) = 1;
+    }
+  }
 }
 
 // Parareal coarse sweep, one CTA per sample; slice states lane-major

@@ -175,7 +175,10 @@ struct DirectLane {
   double* b;               // FP64 right-hand side [n] (mixed)
   int32_t* status_out;     // MQS_ST_* bits of this lane (or-ed)
   double *a0, *a1, *y, *w; // lane vectors [n] (lane-major)
-  double* qoi_out;         // raw QoI sum of the run
+  double* qoi_out;         // raw QoI sum of the run, times qoi_scale
+  double qoi_scale;        // 1 for the raw sum; 1/T or 1/N to write the finished QoI
+  int32_t* done_flag;      // set to 1 (system-wide visible, after qoi_out and status) when
+                           // the lane has finished (one-CTA kernels; nullptr: none)
   int64_t vcol;            // value column (sample) of M / K values
   double amp[kMaxPhases], phase[kMaxPhases];
   double dt, t0;
@@ -221,6 +224,10 @@ struct DirectChain {
   int32_t M, s_first, s_begin, s_end, steps_per_slice, first_sweep;
   double *jump2, *norm2;   // [samples][M] of iteration k
 };
+
+// mqs_api.cu: a context's mesh (nullptr if the id is invalid) and device
+const MeshDev* ctx_mesh(mqs_ctx* ctx, int id);
+int ctx_device(mqs_ctx* ctx);
 
 // mqs_direct.cu
 template <typename T>

@@ -32,6 +32,7 @@ MQS_QOI_ENERGY, MQS_QOI_JOULE = 0, 1
 MQS_ST_NOTCONV, MQS_ST_NONFINITE, MQS_ST_NOTSPD, MQS_ST_TIMEOUT = 1, 2, 4, 8
 MQS_SOLVER_PCG, MQS_SOLVER_BANDED = 0, 1
 MQS_TEST_HOOK_STALL = 1
+MQS_REQ_LEVEL, MQS_REQ_SLICE = 0, 1
 
 _lib = None
 _P = C.c_void_p
@@ -67,6 +68,13 @@ _SIGS = {
                                         _P, _P]),
     "mqs_set_test_hook": (C.c_int, [_P, _i32]),
     "mqs_lane_slots": (C.c_int, [_P, _i32, C.POINTER(_i32)]),
+    "mqs_server_create": (C.c_int, [_P, _i64, _i32, _i32, _f64, C.POINTER(_P)]),
+    "mqs_server_destroy": (C.c_int, [_P]),
+    "mqs_server_submit": (C.c_int, [_P, _i32, _i32, _P, _i32, _i32, _f64, _f64, _i32, _f64, _i32,
+                                    _i64, _P, _P, C.POINTER(_i64)]),
+    "mqs_server_progress": (C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i32)]),
+    "mqs_server_footprint": (C.c_int, [_P, _i32, _i32, _i32, C.POINTER(_i64)]),
+    "mqs_server_poll": (C.c_int, [_P, _i32, _P, _P, _P, _P, C.POINTER(_i32)]),
     "mqs_free_batch": (C.c_int, [_P, _i32]),
     "mqs_free_mesh": (C.c_int, [_P, _i32]),
 }
@@ -280,6 +288,102 @@ def mqs_lane_slots(ctx, precision=MQS_FP64) -> int:
 
 def mqs_set_test_hook(ctx, hook):
     _check("mqs_set_test_hook", load().mqs_set_test_hook(ctx, int(hook)))
+
+
+def mqs_server_create(ctx, hbm_budget=0, n_streams=8, max_batch_lanes=608, freq_hz=50.0):
+    out = _P()
+    _check("mqs_server_create", load().mqs_server_create(ctx, int(hbm_budget), n_streams,
+                                                         max_batch_lanes, freq_hz, C.byref(out)))
+    return out.value
+
+
+def mqs_server_destroy(srv):
+    _check("mqs_server_destroy", load().mqs_server_destroy(srv))
+
+
+def mqs_server_submit(srv, mesh_id, params, kind, qoi_kind, t0, dt, n_steps, dt_prev=0.0,
+                      n_steps_prev=0, k0=0, a_init=None, a_out=None) -> int:
+    p = _host(params, np.float64)
+    ai = None if a_init is None else _host(a_init, np.float64)
+    rid = _i64()
+    _check("mqs_server_submit", load().mqs_server_submit(
+        srv, mesh_id, p.size, _ptr(p), kind, qoi_kind, t0, dt, n_steps, dt_prev, n_steps_prev, k0,
+        _ptr(ai) if ai is not None else None, _ptr(a_out) if a_out is not None else None,
+        C.byref(rid)))
+    return rid.value
+
+
+def mqs_server_footprint(srv, mesh_id, qoi_kind, lanes) -> int:
+    out = _i64()
+    _check("mqs_server_footprint", load().mqs_server_footprint(srv, mesh_id, qoi_kind, lanes,
+                                                               C.byref(out)))
+    return out.value
+
+
+def mqs_server_progress(srv):
+    inf, q = _i32(), _i32()
+    _check("mqs_server_progress", load().mqs_server_progress(srv, C.byref(inf), C.byref(q)))
+    return inf.value, q.value
+
+
+def mqs_server_poll(srv, max_n=4096):
+    ids = np.zeros(max_n, dtype=np.int64)
+    qoi = np.zeros((max_n, 2))
+    st = np.zeros(max_n, dtype=np.int32)
+    tm = np.zeros((max_n, 3))
+    cnt = _i32()
+    _check("mqs_server_poll", load().mqs_server_poll(srv, max_n, _ptr(ids), _ptr(qoi), _ptr(st),
+                                                     _ptr(tm), C.byref(cnt)))
+    c = cnt.value
+    return ids[:c], qoi[:c], st[:c], tm[:c]
+
+
+class Server:
+    """Request server on a context (mqs_server_*): submit level samples and
+    Parareal slices, call progress() often, collect results with poll()."""
+
+    def __init__(self, ctx, hbm_budget=0, n_streams=8, max_batch_lanes=608, freq_hz=50.0):
+        self.h = mqs_server_create(ctx.h, hbm_budget, n_streams, max_batch_lanes, freq_hz)
+
+    def close(self):
+        if self.h:
+            mqs_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, mesh_id, params, kind, qoi_kind, t0, dt, n_steps, **kw):
+        return mqs_server_submit(self.h, mesh_id, params, kind, qoi_kind, t0, dt, n_steps, **kw)
+
+    def progress(self):
+        return mqs_server_progress(self.h)
+
+    def footprint(self, mesh_id, qoi_kind, lanes):
+        return mqs_server_footprint(self.h, mesh_id, qoi_kind, lanes)
+
+    def poll(self, max_n=4096):
+        return mqs_server_poll(self.h, max_n)
+
+    def drain(self, sleep_s=0.0005, timeout_s=600.0):
+        """progress() until nothing is queued or in flight; all results."""
+        import time
+        out = {}
+        t0 = time.time()
+        while True:
+            inf, q = self.progress()
+            for i, qq, st, tm in zip(*self.poll()):
+                out[int(i)] = (qq.copy(), int(st), tm.copy())
+            if inf == 0 and q == 0:
+                for i, qq, st, tm in zip(*self.poll()):
+                    out[int(i)] = (qq.copy(), int(st), tm.copy())
+                return out
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(sleep_s)
 
 
 def mqs_free_batch(ctx, batch):

@@ -178,7 +178,8 @@ def plan_finest_level(N_L, C_L, C_prev, slots, n_steps, coarse_factor, max_slice
 # ---------------------------------------------------------------- adaptive MLMC
 def run_adaptive_mlmc(ctx, mesh_id, sampler, dts, t_end, rmse_target, n_pilot=16,
                       qoi_kind=1, solver=None, chunk=1024, max_per_level=1 << 20,
-                      parareal=False, par_tol=1e-8, lane_slots=None, plan_out=None, **prop):
+                      parareal=False, par_tol=1e-8, lane_slots=None, plan_out=None,
+                      n_min_per_level=None, **prop):
     """Sequential-level MLMC with run-time variance estimates (Sec. II-B).
 
     sampler(level, first, n) -> [n, n_params] parameters of samples
@@ -194,6 +195,8 @@ def run_adaptive_mlmc(ctx, mesh_id, sampler, dts, t_end, rmse_target, n_pilot=16
     Parareal (coarse propagator = level L-2, tolerance par_tol), else
     sequentially.  plan_out (a dict) receives the decision: slots, n_c,para,
     slices, the coarse factor and the Parareal iterations of each batch.
+    n_min_per_level: optional lower bounds on N_l (e.g. to keep a minimum of
+    finest-level samples for a bias estimate).
 
     Returns (estimate, rmse, N_l, levels [N, mean, var]).  All solves run
     through the library's C ABI.
@@ -230,7 +233,8 @@ def run_adaptive_mlmc(ctx, mesh_id, sampler, dts, t_end, rmse_target, n_pilot=16
         variances.append(max(float(lv[l, 2]), 1e-300))
         # size the levels seen so far; only this level can still grow
         N = allocate_samples(variances, cost[:l + 1], rmse_target, n_min=n_pilot)
-        target = int(min(max(N[l], n_pilot), max_per_level))
+        floor_l = n_min_per_level[l] if n_min_per_level is not None else 0
+        target = int(min(max(N[l], n_pilot, floor_l), max_per_level))
         slices, cf = 1, 1
         if parareal and l == L - 1 and L >= 3 and target > done[l]:
             slots = lane_slots if lane_slots is not None else ctx.lane_slots(
