@@ -712,22 +712,33 @@ int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
   return MQS_OK;
 }
 
-// Cluster size of the FP64 stepping kernels with the work vector in shared
-// memory; 0 selects the one-CTA kernels of mqs_direct.cu (mixed precision,
-// work vector in L2).  The widest split (8, 4, 2 CTAs per lane) whose clusters
-// all fit the SMs in one wave; with more lanes, 2 CTAs per lane in several
-// waves.  Measured on the 20k-node annulus: one lane (the coarse sweep) steps
-// fastest on 8 CTAs; 64 lanes on 2 CTAs each (2.55 ms per step); the
-// one-CTA form of these kernels (8 ms per step) and the one-CTA kernel of
-// mqs_direct.cu (7 ms) lose to 2 CTAs per lane even at two waves.
+// Cluster size of the FP64 stepping kernels (each CTA keeps its own rows of
+// the work vector and a ring of recently solved rows in shared memory); 0
+// selects the one-CTA kernels of mqs_direct.cu (mixed precision, and batches
+// of at least two lanes per SM whose work vectors live in L2).  The widest
+// split (8, 4, 2 CTAs per lane) whose clusters all fit the SMs in one wave;
+// with more lanes, the narrowest split that fits shared memory (2 on the 20k
+// annulus, 4 on the 80k annulus) in several waves.  Meshes too large for a
+// one-CTA work vector in shared memory always take the cluster kernels.
+// Measured on the 20k-node annulus: one lane (the coarse sweep) steps fastest
+// on 8 CTAs; 64 lanes on 2 CTAs each (2.55 ms per step); the one-CTA form of
+// these kernels (8 ms per step) and the one-CTA kernel of mqs_direct.cu (7 ms)
+// lose to 2 CTAs per lane even at two waves.
 // env MQS_DIRECT_CLUSTER=0/1/2/4/8 forces a choice.
-int direct_cluster(const MeshDev& m, int lanes, int n_sm, const DirectConst& kc) {
-  if (kc.mixed || !kc.w_in_smem || m.n_free > cluster_max_n()) return 0;
+int direct_cluster(const MeshDev& m, int lanes, int n_sm, bool mixed, bool wide) {
+  if (mixed) return 0;
+  const int n = m.n_free, bw = m.bw;
   const int forced = env_int("MQS_DIRECT_CLUSTER", -1);
-  if (forced == 0 || forced == 1 || forced == 2 || forced == 4 || forced == 8) return forced;
+  if (forced == 0) return 0;
+  if ((forced == 1 || forced == 2 || forced == 4 || forced == 8) && cluster_fits(n, bw, forced))
+    return forced;
+  const bool big = n > direct_smem_max_n(0);
+  if (!wide && !big) return 0;
   for (int cl : {8, 4, 2})
-    if (lanes * cl <= n_sm && lanes <= cluster_max_active(cl, m.n_free)) return cl;
-  return cluster_max_active(2, m.n_free) > 0 ? 2 : 0;
+    if (lanes * cl <= n_sm && lanes <= cluster_max_active(cl, n, bw)) return cl;
+  for (int cl : {2, 4, 8})
+    if (cluster_max_active(cl, n, bw) > 0) return cl;
+  return 0;
 }
 
 // lanes: CTAs of the launch; big batches run 256-thread CTAs with the work
@@ -756,7 +767,7 @@ DirectConst direct_const(const MeshDev& m, const Batch& b, int lanes, const Ctx&
   kc.mixed = mixed ? 1 : 0;
   kc.tol2 = tol * tol;
   kc.max_sweeps = max_sweeps;
-  kc.cluster = direct_cluster(m, lanes, n_sm, kc);
+  kc.cluster = direct_cluster(m, lanes, n_sm, mixed, wide);
   kc.stall_test = c.test_hook == MQS_TEST_HOOK_STALL ? 1 : 0;
   return kc;
 }

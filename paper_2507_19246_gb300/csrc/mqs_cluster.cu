@@ -233,6 +233,23 @@ __device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr,
   return acc;
 }
 
+// Rows of the solved-row ring: a power of two of at least bw + 256.  While
+// the band products of round j read rows down to (first row of block j) - bw,
+// the exchange warps can have stored at most the blocks up to j - 1 (they
+// wait for round j's pre values, which need round j's band products): a span
+// of bw + 64 rows, so bw + 256 leaves slack.
+__host__ __device__ inline int cluster_ring_rows(int bw) {
+  int r = 256;
+  while (r < bw + 4 * 64) r <<= 1;
+  return r;
+}
+
+// Own rows per CTA: R = 64/CL of each 64-row block.
+template <int CL>
+__host__ __device__ inline int own_rows(int n) {
+  return ((n + 63) / 64) * (64 / CL);
+}
+
 // One GEMV work item of a lane: cnt band values at LB[off + j*step], each
 // multiplied by w[w0 + j*wstep].
 struct GemvDesc {
@@ -251,7 +268,13 @@ struct Subst {
   const double* __restrict__ C2;   // [b][r][t]
   const double* __restrict__ D1;   // D1_b^T: [b][t][r]
   const double* __restrict__ D2;   // D2_b^T: [b][t][r]
-  double* w;
+  // work vector: this CTA's own rows of every block (own[b * R + t] = row
+  // b*64 + q*R + t) and a ring of the most recently solved rows of all CTAs
+  // (row r at ring[r & ring_mask]); band products read only rows within the
+  // bandwidth of the block being solved, so the ring holds them
+  double* own;
+  double* ring;
+  int ring_mask;
   CSmem<CL>& sm;
   int n, bw, W, nblk, q;
   // lane roles
@@ -263,9 +286,11 @@ struct Subst {
   int64_t rounds = 0;    // substitution rounds completed (sets the mbarrier phase parity)
   bool stall = false;    // test hook (one-CTA form): the first wait is on a count nothing reaches
 
-  __device__ Subst(const DirectLane& D, double* w_, CSmem<CL>& sm_, int n_, int bw_, int q_)
-      : LB(D.LB), B(D.B64), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), w(w_), sm(sm_), n(n_),
-        bw(bw_), W(bw_ + 1), nblk((n_ + kB - 1) / kB), q(q_) {
+  __device__ Subst(const DirectLane& D, double* own_, double* ring_, int ring_rows,
+                   CSmem<CL>& sm_, int n_, int bw_, int q_)
+      : LB(D.LB), B(D.B64), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), own(own_), ring(ring_),
+        ring_mask(ring_rows - 1), sm(sm_), n(n_), bw(bw_), W(bw_ + 1),
+        nblk((n_ + kB - 1) / kB), q(q_) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     gw = warp - S::GW0;
@@ -285,10 +310,17 @@ struct Subst {
   __device__ bool is_pre() const { return warp >= S::P0 && warp < S::P0 + S::NP; }
   __device__ bool is_gemv() const { return warp >= S::GW0 && warp < S::GW0 + S::GW; }
   __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
-  // own row t of block blk from the copy (0 past n)
+  // own row t of block blk (0 past n)
   __device__ double own_val(int blk, int t) const {
     const int row = blk * kB + q * S::R + t;
-    return row < n ? w[row] : 0.0;
+    return row < n ? own[blk * S::R + t] : 0.0;
+  }
+  __device__ double ring_at(int row) const { return ring[row & ring_mask]; }
+  // a solved row into the ring, and into the own rows if it is one of them
+  __device__ void put_solved(int row, double v) {
+    ring[row & ring_mask] = v;
+    const int t = (row & (kB - 1)) - q * S::R;
+    if (t >= 0 && t < S::R) own[(row / kB) * S::R + t] = v;
   }
   // sum over the lanes of a row (lanes of a row differ in the bits above rw)
   template <int rw>
@@ -354,14 +386,15 @@ struct Subst {
 #pragma unroll
     for (int k = 0; k < kPF; k += 2) {
       if (k >= cmax) break;
-      const double x0 = k < cur.cnt ? w[cur.w0 + k * cur.wstep] : 0.0;
+      const double x0 = k < cur.cnt ? ring_at(cur.w0 + k * cur.wstep) : 0.0;
       acc0 = fma(pf[k], x0, acc0);
       if (k + 1 >= cmax) break;
-      const double x1 = k + 1 < cur.cnt ? w[cur.w0 + (k + 1) * cur.wstep] : 0.0;
+      const double x1 = k + 1 < cur.cnt ? ring_at(cur.w0 + (k + 1) * cur.wstep) : 0.0;
       acc1 = fma(pf[k + 1], x1, acc1);
     }
     for (int k = kPF; k < cmax; ++k)
-      if (k < cur.cnt) acc0 = fma(__ldg(LB + cur.off + k * cur.step), w[cur.w0 + k * cur.wstep], acc0);
+      if (k < cur.cnt)
+        acc0 = fma(__ldg(LB + cur.off + k * cur.step), ring_at(cur.w0 + k * cur.wstep), acc0);
     cur = gemv_desc(j + 1);
     gemv_load(cur, pf);
     double acc = acc0 + acc1;
@@ -374,14 +407,15 @@ struct Subst {
       if (S::H > 4) acc += __shfl_xor_sync(kFull, acc, 16);
       if (f_g == 0 && f_h == 0) {
         const int row = j * kB + q * S::R + f_t;
-        sj[f_t] = row < n ? w[row] - acc : 0.0;
+        sj[f_t] = row < n ? own[j * S::R + f_t] - acc : 0.0;
       }
     } else {
 #pragma unroll
       for (int o = S::TB; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
       if (b_kg == 0) {
-        const int row = (2 * nblk - 1 - j) * kB + q * S::R + b_t;
-        sj[b_t] = row < n ? w[row] - acc : 0.0;
+        const int bt = 2 * nblk - 1 - j;
+        const int row = bt * kB + q * S::R + b_t;
+        sj[b_t] = row < n ? own[bt * S::R + b_t] - acc : 0.0;
       }
     }
   }
@@ -463,7 +497,7 @@ struct Subst {
         for (int t = gt; t < S::R; t += S::GW * 32)
           if (j < G && j != nblk) {
             const int row = j * kB + q * S::R + t;
-            sm.s[j & 3][t] = row < n ? w[row] : 0.0;
+            sm.s[j & 3][t] = row < n ? own[j * S::R + t] : 0.0;
           }
       if constexpr (CL == 1) {
         // test hook: a wait that runs out of polls sets the error flag; every
@@ -527,7 +561,7 @@ struct Subst {
             for (int k = 0; k + span < NV; k += 2 * span) v[k] += v[k + span];
           const double acc = row_sum<S::RW>(v[0]);
           const int row = bp * kB + x_r;
-          if (x_g == 0 && row < n) w[row] = acc;
+          if (x_g == 0 && row < n) put_solved(row, acc);
         }
         if (g == G) break;
         group_sync(1, S::NX * 32);
@@ -554,7 +588,7 @@ struct Subst {
         const double v = row_sum<S::RW>(v0 + v1);
         if constexpr (CL == 1) {
           const int row = b * kB + x_r;
-          if (x_g == 0 && row < n) w[row] = v;
+          if (x_g == 0 && row < n) put_solved(row, v);
         } else {
           const uint32_t la = smem_addr(&sm.V[g & 1][q][x_r]);
           const uint32_t lm = smem_addr(&sm.mbar[g & 1]);
@@ -662,7 +696,7 @@ __device__ int boundary_flags(CSmem<CL>& sm, const DirectConst& kc, unsigned q, 
 template <int CL>
 __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
                                     const double* a_init, int n_steps, int64_t k0, unsigned q,
-                                    Subst<CL>& sub, double* w, bool want_qoi, int& left) {
+                                    Subst<CL>& sub, double* own_w, bool want_qoi, int& left) {
   left = 0;
   if (kc.stop) {   // a launch queued behind the iteration that met the stopping rule
     left = boundary_flags<CL>(sub.sm, kc, q, 1);
@@ -710,7 +744,7 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
 #pragma unroll
       for (int ph = 0; ph < kMaxPhases; ++ph)
         if (ph < kc.n_phases) f = fma(gph[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
-      w[pi] = fma(y[i], inv_dt, f) * __ldg(D.invd + pi);     // D^-1 b, b = M a_k / dt + f
+      own_w[idx] = fma(y[i], inv_dt, f) * __ldg(D.invd + pi);   // D^-1 b, b = M a_k / dt + f
     }
     __syncthreads();
     sub.run(pf);
@@ -718,7 +752,7 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
       const int pi = own.row(idx);
       if (pi >= n) continue;
       const int i = __ldg(kc.perm + pi);
-      a1[i] = w[pi] * __ldg(D.invd + pi);                    // x = D^-1 u
+      a1[i] = own_w[idx] * __ldg(D.invd + pi);                 // x = D^-1 u
     }
     // a1 complete for y = M a1; the whole cluster leaves here together after
     // an expired wait or a cancellation
@@ -758,15 +792,17 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
                                                             DirectConst kc) {
   __shared__ CSmem<CL> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  double* w = reinterpret_cast<double*>(dyn_smem);
+  double* own = reinterpret_cast<double*>(dyn_smem);
+  const int ring_rows = cluster_ring_rows(kc.bw);
+  double* ring = own + own_rows<CL>(kc.n);
   const unsigned q = CL > 1 ? cluster_rank() : 0u;
   const DirectLane D = lanes[blockIdx.x / CL];
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D, w, sm, kc.n, kc.bw, (int)q);
+  Subst<CL> sub(D, own, ring, ring_rows, sm, kc.n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
   const double* init = D.init_from_a0 ? (D.a_init ? D.a_init : D.a0) : nullptr;
   int left = 0;
-  const double part = cluster_integrate<CL>(kc, D, init, D.n_steps, D.k0, q, sub, w, true, left);
+  const double part = cluster_integrate<CL>(kc, D, init, D.n_steps, D.k0, q, sub, own, true, left);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
   if (threadIdx.x == 0 && q == 0)
     D.qoi_out[0] = (kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s) * D.qoi_scale;
@@ -780,7 +816,9 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
                                                         DirectConst kc, DirectChain ch) {
   __shared__ CSmem<CL> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  double* w = reinterpret_cast<double*>(dyn_smem);
+  double* own_w = reinterpret_cast<double*>(dyn_smem);
+  const int ring_rows = cluster_ring_rows(kc.bw);
+  double* ring = own_w + own_rows<CL>(kc.n);
   const unsigned q = CL > 1 ? cluster_rank() : 0u;
   const DirectLane D = lanes[blockIdx.x / CL];
   const int n = kc.n;
@@ -788,7 +826,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   const int n_own = own.count();
   const int sample = D.sample;
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D, w, sm, n, kc.bw, (int)q);
+  Subst<CL> sub(D, own_w, ring, ring_rows, sm, n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
   const int s_stop = min(ch.s_end, ch.M - 1);
   for (int s = ch.s_begin; s < s_stop; ++s) {
@@ -796,7 +834,7 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
     const double* U0 = s == ch.s_first ? ch.U_prev : ch.U_cur;
     int left = 0;
     cluster_integrate<CL>(kc, D, U0 + base, ch.steps_per_slice,
-                          (int64_t)s * ch.steps_per_slice, q, sub, w, false, left);
+                          (int64_t)s * ch.steps_per_slice, q, sub, own_w, false, left);
     if (left) break;   // every CTA of the cluster leaves at the same slice
     double j2 = 0.0, u2 = 0.0;
     for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
@@ -901,9 +939,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __res
 // ---------------------------------------------------------------- band Cholesky on a cluster
 // Right-looking band Cholesky of one factor on a cluster of NC CTAs (the same
 // result and layout as the one-CTA k_band_chol: L in place, L(j, j) on the
-// diagonal, invd = 1 / L(j, j)).  Row i belongs to CTA i mod NC, which keeps
-// it in a shared-memory ring from the column where it enters the band window
-// until it is final, then writes it back once.  Per column j: every CTA
+// diagonal, invd = 1 / L(j, j); the products of the trailing updates summed in
+// a separate accumulator S and subtracted once, as there).  Row i belongs to
+// CTA i mod NC, which keeps it (and its S row) in a shared-memory ring from
+// the column where it enters the band window until it is final, then writes
+// it back once.  Per column j: every CTA
 // scales its rows' entry of column j and sends it to every CTA's column
 // buffer; the owner of row j + 1 forms that row's pivot and sends its
 // reciprocal; all sends are asynchronous DSMEM stores counted on the
@@ -917,8 +957,8 @@ __device__ __forceinline__ int count_mod(int a, int b, int r, int nc) {   // #{i
 template <int NC>
 struct CholRing {
   static int slots(int bw) { return (bw + 1 + NC - 1) / NC + 2; }
-  static size_t bytes(int bw) {
-    return sizeof(double) * ((size_t)slots(bw) * (bw + 1) + 2 * (size_t)std::max(bw, 1));
+  static size_t bytes(int bw) {   // rows and S rows of the ring, two column buffers
+    return sizeof(double) * (2 * (size_t)slots(bw) * (bw + 1) + 2 * (size_t)std::max(bw, 1));
   }
 };
 
@@ -930,7 +970,8 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
   const int W = bw + 1;
   const int RING = (bw + 1 + NC - 1) / NC + 2;
   double* ring = reinterpret_cast<double*>(chol_smem);   // [RING][W]: own rows of the window
-  double* col = ring + (size_t)RING * W;                  // [2][bw]: column j of L below the diagonal
+  double* sring = ring + (size_t)RING * W;                // [RING][W]: their accumulated products
+  double* col = sring + (size_t)RING * W;                 // [2][bw]: column j of L below the diagonal
   __shared__ double piv[2];                               // 1 / L(j, j) by column parity
   __shared__ double l00;
   __shared__ unsigned long long mb[2];
@@ -941,10 +982,15 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
   double* invd = invd_all + (int64_t)f * n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto row_of = [&](int i) -> double* { return ring + (size_t)((i / NC) % RING) * W; };
+  auto srow_of = [&](int i) -> double* { return sring + (size_t)((i / NC) % RING) * W; };
   auto load_row = [&](int i) {          // all threads of the CTA
     const double* src = LB + (int64_t)i * W;
     double* dst = row_of(i);
-    for (int d = threadIdx.x; d < W; d += kNT) dst[d] = src[d];
+    double* sd = srow_of(i);
+    for (int d = threadIdx.x; d < W; d += kNT) {
+      dst[d] = src[d];
+      sd[d] = 0.0;
+    }
   };
   auto store_row = [&](int i) {
     const double* src = row_of(i);
@@ -995,7 +1041,8 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
     if (threadIdx.x < n_own) {
       const int i = first + NC * threadIdx.x;
       double* row = row_of(i);
-      const double l = row[j - i + bw] * inv;
+      double* srw = srow_of(i);
+      const double l = (row[j - i + bw] - srw[j - i + bw]) * inv;
       row[j - i + bw] = l;
       const uint32_t la = smem_addr(cj + (i - j - 1));
       const uint32_t lm = smem_addr(&mb[par]);
@@ -1006,7 +1053,8 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
           st_async(map_rank(la, p), l, map_rank(lm, p));
       }
       if (i == j + 1) {   // this CTA owns row j + 1: its pivot
-        double d = fma(-l, l, row[bw]);   // the rank-1 update of the diagonal, as in k_band_chol
+        // the last product of the diagonal, then A - S, as in k_band_chol
+        double d = row[bw] - fma(l, l, srw[bw]);
         if (!(d > 0.0)) {
           bad[f] = 1;
           d = 1.0;
@@ -1032,8 +1080,8 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
       const int i = first + NC * k;
       if (i == j + 1) continue;
       const double li = cj[i - j - 1];
-      double* row = row_of(i) + bw - i;                 // row[c] = A(i, c)
-      for (int c = j + 1 + lane; c <= i; c += 32) row[c] = fma(-li, cj[c - j - 1], row[c]);
+      double* srw = srow_of(i) + bw - i;                // srw[c] = S(i, c)
+      for (int c = j + 1 + lane; c <= i; c += 32) srw[c] = fma(li, cj[c - j - 1], srw[c]);
     }
     // row j + 1 is final: write it back; row j + 1 + bw enters the window at column j + 1
     if (j + 1 < n && (j + 1) % NC == rho) store_row(j + 1);
@@ -1050,7 +1098,18 @@ const void* propagate_fn() { return reinterpret_cast<const void*>(&k_cluster_pro
 template <int CL>
 const void* chain_fn() { return reinterpret_cast<const void*>(&k_cluster_chain<CL>); }
 
-size_t cluster_smem(int n) { return (size_t)n * sizeof(double); }
+template <int CL>
+size_t cluster_smem_t(int n, int bw) {
+  return (size_t)(own_rows<CL>(n) + cluster_ring_rows(bw)) * sizeof(double);
+}
+size_t cluster_smem(int n, int bw, int CL) {
+  switch (CL) {
+    case 1: return cluster_smem_t<1>(n, bw);
+    case 2: return cluster_smem_t<2>(n, bw);
+    case 4: return cluster_smem_t<4>(n, bw);
+    default: return cluster_smem_t<8>(n, bw);
+  }
+}
 
 template <int CL>
 int set_attrs(size_t smem) {
@@ -1106,23 +1165,29 @@ int max_active_t(size_t smem) {
 
 }  // namespace
 
-int cluster_max_n() {
-  const size_t fixed = std::max(std::max(sizeof(CSmem<1>), sizeof(CSmem<2>)),
-                                std::max(sizeof(CSmem<4>), sizeof(CSmem<8>)));
-  return (int)((227 * 1024 - fixed - 1024) / sizeof(double));
+// The own rows and the ring fit next to the static shared memory (227 KB per CTA).
+bool cluster_fits(int n, int bw, int CL) {
+  size_t fixed = sizeof(CSmem<8>);
+  switch (CL) {
+    case 1: fixed = sizeof(CSmem<1>); break;
+    case 2: fixed = sizeof(CSmem<2>); break;
+    case 4: fixed = sizeof(CSmem<4>); break;
+  }
+  return cluster_smem(n, bw, CL) + fixed + 1024 <= 227 * 1024;
 }
 
-int cluster_max_active(int CL, int n) {
+int cluster_max_active(int CL, int n, int bw) {
   static std::mutex mu;
   static int cache[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
-  static int cache_n[4] = {-1, -1, -1, -1};
+  static int64_t cache_n[4] = {-1, -1, -1, -1};
   const int slot = CL == 1 ? 0 : CL == 2 ? 1 : CL == 4 ? 2 : CL == 8 ? 3 : -1;
-  if (slot < 0) return 0;
+  if (slot < 0 || !cluster_fits(n, bw, CL)) return 0;
   int dev = 0;
   cudaGetDevice(&dev);
+  const int64_t key = (int64_t)n * 65536 + bw;
   std::lock_guard<std::mutex> lk(mu);
-  if (cache_n[slot] == n && cache[slot][0] == dev) return cache[slot][1];
-  const size_t smem = cluster_smem(n);
+  if (cache_n[slot] == key && cache[slot][0] == dev) return cache[slot][1];
+  const size_t smem = cluster_smem(n, bw, CL);
   int r = 0;
   switch (CL) {
     case 1: r = max_active_t<1>(smem); break;
@@ -1130,7 +1195,7 @@ int cluster_max_active(int CL, int n) {
     case 4: r = max_active_t<4>(smem); break;
     case 8: r = max_active_t<8>(smem); break;
   }
-  cache_n[slot] = n;
+  cache_n[slot] = key;
   cache[slot][0] = dev;
   cache[slot][1] = r;
   return r;
@@ -1165,8 +1230,8 @@ int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, 
   return MQS_OK;
 }
 int band_chol_cluster_size() { return 8; }
-// The cluster kernel keeps the window's rows in shared memory: bandwidths up
-// to ~440 on 8 CTAs.
+// The cluster kernel keeps the window's rows and their accumulated products in
+// shared memory: bandwidths up to ~300 on 8 CTAs.
 bool band_chol_cluster_fits(int bw) { return CholRing<8>::bytes(bw) <= 200 * 1024; }
 
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
@@ -1186,7 +1251,7 @@ int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double*
 
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  const size_t smem = cluster_smem(kc.n);
+  const size_t smem = cluster_smem(kc.n, kc.bw, kc.cluster);
   switch (kc.cluster) {
     case 1: return launch_cl<1>(propagate_fn<1>(), n_lanes, smem, st, d_lanes, kc);
     case 2: return launch_cl<2>(propagate_fn<2>(), n_lanes, smem, st, d_lanes, kc);
@@ -1200,7 +1265,7 @@ int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc
 int launch_cluster_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                          const DirectChain& ch, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
-  const size_t smem = cluster_smem(kc.n);
+  const size_t smem = cluster_smem(kc.n, kc.bw, kc.cluster);
   switch (kc.cluster) {
     case 1: return launch_cl<1>(chain_fn<1>(), n_lanes, smem, st, d_lanes, kc, ch);
     case 2: return launch_cl<2>(chain_fn<2>(), n_lanes, smem, st, d_lanes, kc, ch);

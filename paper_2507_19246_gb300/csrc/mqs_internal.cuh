@@ -249,8 +249,8 @@ int band_chol_cluster_size();
 bool band_chol_cluster_fits(int bw);
 int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
                double* D1, double* D2, cudaStream_t st);
-int cluster_max_n();
-int cluster_max_active(int CL, int n);
+bool cluster_fits(int n, int bw, int CL);          // own rows + ring fit a CTA's shared memory
+int cluster_max_active(int CL, int n, int bw);      // resident clusters (0: does not fit)
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
 int launch_cluster_chain(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc,
                          const DirectChain& ch, cudaStream_t st);

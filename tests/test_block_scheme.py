@@ -95,9 +95,24 @@ def block_arrays(lb, n, bw):
     return out
 
 
-def substitute(lb, arr, n, bw, w_in, cl):
+def ring_rows_of(bw):
+    """Rows of the kernels' solved-row ring: a power of two >= bw + 256."""
+    r = 256
+    while r < bw + 4 * 64:
+        r *= 2
+    return r
+
+
+def substitute(lb, arr, n, bw, w_in, cl, ring_rows=None, late_gemv=False):
     """Forward and backward substitution on a cluster of `cl` CTAs, as the
-    kernels do it.  Returns every CTA's copy of the solution."""
+    kernels do it.  Returns every CTA's copy of the solution.
+
+    ring_rows: each CTA keeps only its own rows of the work vector plus a ring
+    of the last ring_rows solved rows (row r in slot r % ring_rows, tagged with
+    r so that reading a row that is not, or no longer, there fails); the
+    returned copies are assembled from the CTAs' own rows.  late_gemv: the band
+    products of round j run as late as the warp hand-offs allow (after block
+    j - 1 is stored), instead of as early (after block j - 3)."""
     r_own = KB // cl
     gw = GW_OF[cl]
     h = 8 * gw // r_own                   # forward chunks per own row
@@ -112,21 +127,51 @@ def substitute(lb, arr, n, bw, w_in, cl):
     shares = [np.full((2, cl, KB), np.nan) for _ in range(cl)]
     ring = [np.full((4, r_own), np.nan) for _ in range(cl)]
     pre = [np.full(KB, np.nan) for _ in range(cl)]
+    own_rows = [Checked(np.full(nblk * r_own, np.nan), f"own{q}") for q in range(cl)]
+    if ring_rows is not None:
+        rvals = [np.full(ring_rows, np.nan) for _ in range(cl)]
+        rtags = [np.full(ring_rows, -1) for _ in range(cl)]
+
+    def put(q, row, v):                   # a solved row: ring (or copy) and own rows
+        if ring_rows is None:
+            copies[q][row] = v
+            return
+        rvals[q][row % ring_rows] = v
+        rtags[q][row % ring_rows] = row
+        t = row % KB - q * r_own
+        if 0 <= t < r_own:
+            own_rows[q][(row // KB) * r_own + t] = v
+
+    def solved(q, row):                   # a solved row of any CTA (band products)
+        if ring_rows is None:
+            return copies[q][row]
+        assert rtags[q][row % ring_rows] == row, ("ring", q, row, rtags[q][row % ring_rows])
+        return rvals[q][row % ring_rows]
+
+    def own_at(q, blk, t):                # own row t of block blk
+        if ring_rows is None:
+            return copies[q][blk * KB + q * r_own + t]
+        v = own_rows[q][blk * r_own + t]
+        assert np.isfinite(v), ("own row not formed", q, blk, t)
+        return v
+
     for q in range(cl):                   # own rows of the right-hand side
         for idx in range(nblk * r_own):
             pi = (idx // r_own) * KB + q * r_own + idx % r_own
             if pi < n:
-                copies[q][pi] = w_in[pi]
+                if ring_rows is None:
+                    copies[q][pi] = w_in[pi]
+                else:
+                    own_rows[q][idx] = w_in[pi]
 
     def block_of(g):
         return g if g < nblk else 2 * nblk - 1 - g
 
     def own(q, blk, t):
         row = blk * KB + q * r_own + t
-        return copies[q][row] if row < n else 0.0
+        return own_at(q, blk, t) if row < n else 0.0
 
     def gemv(q, j):                       # s of round j over the blocks known after round j - 2
-        w = copies[q]
         acc = np.zeros(r_own)
         for warp in range(gw):
             for lane in range(32):
@@ -138,7 +183,7 @@ def substitute(lb, arr, n, bw, w_in, cl):
                         continue
                     c, hi = max(0, i - bw) + 4 * hh + gl, (j - 2) * KB
                     while c < hi:
-                        acc[t] += lbc[i * w_ + (c - i + bw)] * w[c]
+                        acc[t] += lbc[i * w_ + (c - i + bw)] * solved(q, c)
                         c += 4 * h
                 else:                     # column c of block bt, rows of blocks >= bt + 3
                     bt = 2 * nblk - 1 - j
@@ -148,12 +193,12 @@ def substitute(lb, arr, n, bw, w_in, cl):
                         continue
                     k = (bt + 3) * KB + grp
                     while k <= min(n - 1, c + bw):
-                        acc[t] += lbc[k * w_ + (c - k + bw)] * w[k]
+                        acc[t] += lbc[k * w_ + (c - k + bw)] * solved(q, k)
                         k += kg
         blk = block_of(j)
         for t in range(r_own):
             row = blk * KB + q * r_own + t
-            ring[q][j & 3, t] = w[row] - acc[t] if row < n else 0.0
+            ring[q][j & 3, t] = own_at(q, blk, t) - acc[t] if row < n else 0.0
 
     def pre_of(q, g1):                    # B s - C2 y_{b-2} (forward) or B^T s - D2^T u_{b+2}
         b1 = block_of(g1)
@@ -179,7 +224,7 @@ def substitute(lb, arr, n, bw, w_in, cl):
             if j < g_end and j != nblk:
                 for t in range(r_own):
                     row = j * KB + q * r_own + t
-                    ring[q][j & 3, t] = copies[q][row] if row < n else 0.0
+                    ring[q][j & 3, t] = own_at(q, j, t) if row < n else 0.0
     for g in range(g_end + 1):
         if cl > 1 and g >= 1:             # gather the shares of round g - 1, rank order
             bp = block_of(g - 1)
@@ -188,17 +233,18 @@ def substitute(lb, arr, n, bw, w_in, cl):
                     v = shares[q][(g - 1) & 1, :, r]
                     assert np.all(np.isfinite(v))
                     if bp * KB + r < n:
-                        copies[q][bp * KB + r] = v.sum()
+                        put(q, bp * KB + r, v.sum())
         if g == g_end:
             break
-        if g + 2 < g_end and g + 2 != nblk:
+        j = g if late_gemv else g + 2     # band products as late / as early as allowed
+        if 2 <= j < g_end and j != nblk:
             for q in range(cl):
-                gemv(q, g + 2)
+                gemv(q, j)
         for q in range(cl):
             pre_of(q, g)
         b, fwd = block_of(g), g < nblk
         new_shares = [x.copy() for x in shares]
-        solved = []
+        done_rows = []
         for q in range(cl):
             for r in range(KB):           # v = pre - C1 y_{b-1} or pre - D1^T u_{b+1}
                 v = pre[q][r]
@@ -210,14 +256,25 @@ def substitute(lb, arr, n, bw, w_in, cl):
                         v -= D1[b * KB * KB + tc * KB + r] * own(q, b + 1, t)
                 if cl == 1:
                     if b * KB + r < n:
-                        solved.append((b * KB + r, v))
+                        done_rows.append((b * KB + r, v))
                 else:
                     for p in range(cl):
                         new_shares[p][g & 1, q, r] = v
         shares = new_shares
-        for i, v in solved:
-            copies[0][i] = v
-    return [c.a for c in copies]
+        for i, v in done_rows:
+            put(0, i, v)
+    if ring_rows is None:
+        return [c.a for c in copies]
+    out = []                              # every CTA's own rows, gathered
+    for q in range(cl):
+        full = np.full(n, np.nan)
+        for qq in range(cl):
+            for idx in range(nblk * r_own):
+                pi = (idx // r_own) * KB + qq * r_own + idx % r_own
+                if pi < n:
+                    full[pi] = own_rows[qq].a[idx]
+        out.append(full)
+    return out
 
 
 @pytest.mark.parametrize("cl", [1, 2, 4, 8])
@@ -237,6 +294,23 @@ def test_cluster_substitution_scheme_solves_the_band_system(cl, n, bw):
     for c in copies:
         assert np.allclose(c, u, rtol=1e-10, atol=1e-10)
     assert all(np.array_equal(copies[0], c) for c in copies)   # identical copies
+    # own rows + ring of solved rows, band products as early and as late as
+    # the hand-offs allow: the same values bit for bit
+    for late in (False, True):
+        dist = substitute(lb, arr, n, bw, rhs, cl, ring_rows=ring_rows_of(bw), late_gemv=late)
+        assert all(np.array_equal(copies[0], c) for c in dist), late
+
+
+@pytest.mark.parametrize("cl", [2, 8])
+def test_ring_smaller_than_the_band_fails(cl):
+    """A ring shorter than the rows the band products reach must be caught by
+    the model (the check is not vacuous)."""
+    n, bw = 450, 204
+    rng = np.random.default_rng(5)
+    lt, lb = unit_band(banded_spd(n, bw, rng), bw)
+    arr = block_arrays(lb, n, bw)
+    with pytest.raises(AssertionError):
+        substitute(lb, arr, n, bw, rng.normal(size=n), cl, ring_rows=128, late_gemv=True)
 
 
 def count_mod(a, b, r, nc):
@@ -251,8 +325,10 @@ def cluster_cholesky(a, bw, nc):
     """Band Cholesky on `nc` CTAs as k_band_chol_cl does it: row i owned by
     CTA i mod nc and held in a ring of (bw + 1)/nc + 2 slots from the column
     where it enters the window until it is final, per column the scaled
-    entries and the next pivot sent to every CTA; checks each CTA's received
-    bytes against the count it arms its mbarrier with."""
+    entries and the next pivot sent to every CTA; the products of the
+    trailing updates summed in a separate ring of accumulators S (zeroed when a
+    row enters) and subtracted once, when the row's entry is scaled; checks
+    each CTA's received bytes against the count it arms its mbarrier with."""
     n = a.shape[0]
     w = bw + 1
     slots = (bw + 1 + nc - 1) // nc + 2
@@ -262,6 +338,7 @@ def cluster_cholesky(a, bw, nc):
             g[i * w + (c - i + bw)] = a[i, c]
     out, done = np.full(n * w, np.nan), np.zeros(n, int)
     ring = [np.full((slots, w), np.nan) for _ in range(nc)]
+    sring = [np.full((slots, w), np.nan) for _ in range(nc)]
     held = [[-1] * slots for _ in range(nc)]
     col = [np.full((2, max(bw, 1)), np.nan) for _ in range(nc)]
     piv = [np.full(2, np.nan) for _ in range(nc)]
@@ -270,12 +347,18 @@ def cluster_cholesky(a, bw, nc):
         s = (i // nc) % slots
         assert held[rho][s] == -1 or done[held[rho][s]], ("slot still live", rho, i)
         ring[rho][s] = g[i * w:(i + 1) * w]
+        sring[rho][s] = 0.0
         held[rho][s] = i
 
     def row(rho, i):
         s = (i // nc) % slots
         assert held[rho][s] == i, ("row not in the ring", rho, i)
         return ring[rho][s]
+
+    def srow(rho, i):
+        s = (i // nc) % slots
+        assert held[rho][s] == i, ("row not in the ring", rho, i)
+        return sring[rho][s]
 
     def store(rho, i):
         assert not done[i]
@@ -297,14 +380,14 @@ def cluster_cholesky(a, bw, nc):
             for i in range(j + 1, j + total + 1):
                 if i % nc != rho:
                     continue
-                ri = row(rho, i)
-                l = ri[j - i + bw] * piv[rho][j & 1]
+                ri, si = row(rho, i), srow(rho, i)
+                l = (ri[j - i + bw] - si[j - i + bw]) * piv[rho][j & 1]
                 ri[j - i + bw] = l
                 for p in range(nc):
                     col[p][j & 1, i - j - 1] = l
                     got[p] += 8 * (p != rho)
                 if i == j + 1:                             # the owner of row j + 1: its pivot
-                    lj = np.sqrt(ri[bw] - l * l)
+                    lj = np.sqrt(ri[bw] - (si[bw] + l * l))
                     ri[bw] = lj
                     for p in range(nc):
                         piv[p][(j + 1) & 1] = 1.0 / lj
@@ -317,9 +400,9 @@ def cluster_cholesky(a, bw, nc):
             for i in range(j + 2, j + total + 1):
                 if i % nc != rho:
                     continue
-                ri, li = row(rho, i), col[rho][j & 1, i - j - 1]
+                si, li = srow(rho, i), col[rho][j & 1, i - j - 1]
                 for c in range(j + 1, i + 1):
-                    ri[c - i + bw] -= li * col[rho][j & 1, c - j - 1]
+                    si[c - i + bw] += li * col[rho][j & 1, c - j - 1]
             if j + 1 < n and (j + 1) % nc == rho:
                 store(rho, j + 1)
             if j + 1 + bw < n and (j + 1 + bw) % nc == rho:
