@@ -156,6 +156,7 @@ struct Ctx {
   // factorisation runs beside the coarse one and the first coarse sweep)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_comp0 = nullptr, ev_comp1 = nullptr;   // companion solve beside Parareal
   int n_sm = 1;
   int test_hook = 0;   // MQS_TEST_HOOK_* of mqs_set_test_hook
   std::vector<std::unique_ptr<MeshDev>> meshes;
@@ -194,6 +195,8 @@ struct Ctx {
     for (cudaEvent_t e : ev_fjoin) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_comp0) cudaEventDestroy(ev_comp0);
+    if (ev_comp1) cudaEventDestroy(ev_comp1);
   }
 };
 
@@ -222,6 +225,8 @@ int ensure_side(Ctx& c) {
   if (!c.side) MQS_CUDA_TRY(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
   if (!c.ev_fork) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
   if (!c.ev_join) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+  if (!c.ev_comp0) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_comp0, cudaEventDisableTiming));
+  if (!c.ev_comp1) MQS_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_comp1, cudaEventDisableTiming));
   return MQS_OK;
 }
 
@@ -1555,8 +1560,19 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
                          qoi_scale(b.qoi_kind, nsf, dt_level),
                          fc ? qoi_scale(b.qoi_kind, nsc, dt_prev) : 0.0, b.qoi.as<double>(), st));
     } else {
-      if (fc)
-        MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc, mixed, cg_tol, cg_max_iters));
+      // the companion level-(l-1) solve of each sample runs on the side stream,
+      // beside the Parareal iterations (its factor was formed on the main stream)
+      cudaEvent_t comp_done = nullptr;
+      if (fc) {
+        MQS_CUDA_TRY(cudaEventRecord(ctx->c.ev_comp0, ctx->c.stream));
+        MQS_CUDA_TRY(cudaStreamWaitEvent(ctx->c.side, ctx->c.ev_comp0, 0));
+        {
+          OnSide on(ctx->c);
+          MQS_TRY(run_plain_direct(ctx, b, m, nullptr, 0, fc, nsc, mixed, cg_tol, cg_max_iters));
+          MQS_CUDA_TRY(cudaEventRecord(ctx->c.ev_comp1, ctx->c.side));
+        }
+        comp_done = ctx->c.ev_comp1;
+      }
       FactorSet* fC = factor_set(ctx, b, m, dt_level * coarse_factor, mixed, rc);
       if (!fC) return rc;
       if (fine_ready && fC == ff)   // coarse_factor 1: the coarse sweep uses the fine factor
@@ -1564,6 +1580,7 @@ int mqs_propagate(mqs_ctx* ctx, int32_t batch_id, int32_t level, double dt_level
       MQS_TRY(run_parareal_direct(ctx, b, m, *ff, *fC, nsf, n_slices, coarse_factor,
                                   max_par_iters, par_tol, mixed, cg_tol, cg_max_iters,
                                   par_iters, fine_ready));
+      if (comp_done) MQS_CUDA_TRY(cudaStreamWaitEvent(ctx->c.stream, comp_done, 0));
       b.mode = 4;
       b.M = n_slices;
       MQS_TRY(finish_qoi(b.dpar.qraw.as<double>(), fc ? b.dplain.qraw.as<double>() : nullptr,

@@ -92,3 +92,40 @@ def test_annulus80k_many_lanes_multiwave_is_bitwise_one_lane(setup, monkeypatch)
             out.append((q.copy(), ctx.read_state(b, 0)))
     assert out[0][0][7, 0] == out[1][0][0, 0] and out[0][0][7, 1] == out[1][0][0, 1]
     assert np.array_equal(out[0][1][7], out[1][1][0])
+
+
+def test_annulus80k_combined_mlmc_parareal_K_equals_M_is_sequential(setup):
+    """The combined method (Sec. II-D) on the 80k annulus over a short
+    horizon: three levels, the finest by Parareal with coarse propagator =
+    level 0 (coarse factor 4) and its level-1 companion solve beside it; with
+    tolerance 0 Parareal runs K = M iterations and reproduces the serial fine
+    solve, so the MLMC estimate equals an all-sequential run of the same
+    samples within 1e-10."""
+    mqs, mesh = setup
+    T = configs.PERIOD / 8
+    dts = [configs.level_dt(l) for l in range(3)]
+    N = [4, 2, 2]
+    prm = [params.annulus_samples(N[l], l, seed=83) for l in range(3)]
+    out = []
+    with mqs.Context(0) as ctx:
+        mid = ctx.upload_mesh(mesh)
+        for parareal_on in (True, False):
+            ctx.mlmc_reset(3)
+            for l in range(3):
+                b = ctx.set_samples(mid, prm[l])
+                ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+                ctx.set_time(b, 0.0, T, 50.0, mqs.MQS_QOI_JOULE)
+                kw = (dict(n_slices=8, coarse_factor=4, max_par_iters=8, par_tol=0.0)
+                      if (parareal_on and l == 2) else {})
+                K = ctx.propagate(b, l, dts[l], dt_prev=dts[l - 1] if l else 0.0, **kw)
+                if kw:
+                    assert K == 8
+                q, st = ctx.read_qoi(b)
+                assert not st.any()
+                ctx.mlmc_accumulate(b, l)
+                ctx.free_batch(b)
+            out.append(ctx.mlmc_readout())
+    (lv_p, est_p, rmse_p), (lv_s, est_s, rmse_s) = out
+    assert abs(est_p - est_s) <= 1e-10 * abs(est_s)
+    assert rmse_p == pytest.approx(rmse_s, rel=1e-8)
+    assert np.allclose(lv_p[:, 1], lv_s[:, 1], rtol=1e-9, atol=1e-12 * abs(est_s))
