@@ -258,7 +258,11 @@ struct GemvDesc {
 };
 
 // ---------------------------------------------------------------- substitution
-template <int CL>
+// FULL: every CTA keeps the whole permuted work vector (own = ring = w,
+// indexed by row) -- the layout when n doubles fit a CTA's shared memory;
+// otherwise own rows plus the ring of solved rows (below).  The arithmetic and
+// its order are the same in both.
+template <int CL, bool FULL>
 struct Subst {
   using S = Split<CL>;
   static constexpr int kBB = kB * kB;
@@ -310,17 +314,27 @@ struct Subst {
   __device__ bool is_pre() const { return warp >= S::P0 && warp < S::P0 + S::NP; }
   __device__ bool is_gemv() const { return warp >= S::GW0 && warp < S::GW0 + S::GW; }
   __device__ int block_of(int g) const { return g < nblk ? g : 2 * nblk - 1 - g; }
+  // storage of own row t of block blk
+  __device__ double& own_at(int blk, int t) const {
+    return FULL ? own[blk * kB + q * S::R + t] : own[blk * S::R + t];
+  }
   // own row t of block blk (0 past n)
   __device__ double own_val(int blk, int t) const {
     const int row = blk * kB + q * S::R + t;
-    return row < n ? own[blk * S::R + t] : 0.0;
+    return row < n ? own_at(blk, t) : 0.0;
   }
-  __device__ double ring_at(int row) const { return ring[row & ring_mask]; }
+  // storage index of own node idx (row pi) in the node-wise phases
+  __device__ int own_index(int idx, int pi) const { return FULL ? pi : idx; }
+  __device__ double ring_at(int row) const { return FULL ? own[row] : ring[row & ring_mask]; }
   // a solved row into the ring, and into the own rows if it is one of them
   __device__ void put_solved(int row, double v) {
-    ring[row & ring_mask] = v;
-    const int t = (row & (kB - 1)) - q * S::R;
-    if (t >= 0 && t < S::R) own[(row / kB) * S::R + t] = v;
+    if (FULL) {
+      own[row] = v;
+    } else {
+      ring[row & ring_mask] = v;
+      const int t = (row & (kB - 1)) - q * S::R;
+      if (t >= 0 && t < S::R) own[(row / kB) * S::R + t] = v;
+    }
   }
   // sum over the lanes of a row (lanes of a row differ in the bits above rw)
   template <int rw>
@@ -407,7 +421,7 @@ struct Subst {
       if (S::H > 4) acc += __shfl_xor_sync(kFull, acc, 16);
       if (f_g == 0 && f_h == 0) {
         const int row = j * kB + q * S::R + f_t;
-        sj[f_t] = row < n ? own[j * S::R + f_t] - acc : 0.0;
+        sj[f_t] = row < n ? own_at(j, f_t) - acc : 0.0;
       }
     } else {
 #pragma unroll
@@ -415,7 +429,7 @@ struct Subst {
       if (b_kg == 0) {
         const int bt = 2 * nblk - 1 - j;
         const int row = bt * kB + q * S::R + b_t;
-        sj[b_t] = row < n ? own[bt * S::R + b_t] - acc : 0.0;
+        sj[b_t] = row < n ? own_at(bt, b_t) - acc : 0.0;
       }
     }
   }
@@ -497,7 +511,7 @@ struct Subst {
         for (int t = gt; t < S::R; t += S::GW * 32)
           if (j < G && j != nblk) {
             const int row = j * kB + q * S::R + t;
-            sm.s[j & 3][t] = row < n ? own[j * S::R + t] : 0.0;
+            sm.s[j & 3][t] = row < n ? own_at(j, t) : 0.0;
           }
       if constexpr (CL == 1) {
         // test hook: a wait that runs out of polls sets the error flag; every
@@ -693,10 +707,10 @@ __device__ int boundary_flags(CSmem<CL>& sm, const DirectConst& kc, unsigned q, 
 // `left` receives the step-boundary flags that ended the run early (1: a wait
 // ran out, 2: the launch was cancelled; 0: all steps ran), the same on every
 // CTA of the cluster.
-template <int CL>
+template <int CL, bool FULL>
 __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
                                     const double* a_init, int n_steps, int64_t k0, unsigned q,
-                                    Subst<CL>& sub, double* own_w, bool want_qoi, int& left) {
+                                    Subst<CL, FULL>& sub, double* own_w, bool want_qoi, int& left) {
   left = 0;
   if (kc.stop) {   // a launch queued behind the iteration that met the stopping rule
     left = boundary_flags<CL>(sub.sm, kc, q, 1);
@@ -744,7 +758,7 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
 #pragma unroll
       for (int ph = 0; ph < kMaxPhases; ++ph)
         if (ph < kc.n_phases) f = fma(gph[ph], __ldg(kc.F + (int64_t)ph * n + i), f);
-      own_w[idx] = fma(y[i], inv_dt, f) * __ldg(D.invd + pi);   // D^-1 b, b = M a_k / dt + f
+      own_w[sub.own_index(idx, pi)] = fma(y[i], inv_dt, f) * __ldg(D.invd + pi);   // D^-1 b
     }
     __syncthreads();
     sub.run(pf);
@@ -752,7 +766,7 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
       const int pi = own.row(idx);
       if (pi >= n) continue;
       const int i = __ldg(kc.perm + pi);
-      a1[i] = own_w[idx] * __ldg(D.invd + pi);                 // x = D^-1 u
+      a1[i] = own_w[sub.own_index(idx, pi)] * __ldg(D.invd + pi);   // x = D^-1 u
     }
     // a1 complete for y = M a1; the whole cluster leaves here together after
     // an expired wait or a cancellation
@@ -787,22 +801,23 @@ __device__ double cluster_integrate(const DirectConst& kc, const DirectLane& D,
   return qacc;
 }
 
-template <int CL>
+template <int CL, bool FULL>
 __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* __restrict__ lanes,
                                                             DirectConst kc) {
   __shared__ CSmem<CL> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   double* own = reinterpret_cast<double*>(dyn_smem);
   const int ring_rows = cluster_ring_rows(kc.bw);
-  double* ring = own + own_rows<CL>(kc.n);
+  double* ring = FULL ? own : own + own_rows<CL>(kc.n);
   const unsigned q = CL > 1 ? cluster_rank() : 0u;
   const DirectLane D = lanes[blockIdx.x / CL];
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D, own, ring, ring_rows, sm, kc.n, kc.bw, (int)q);
+  Subst<CL, FULL> sub(D, own, ring, ring_rows, sm, kc.n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
   const double* init = D.init_from_a0 ? (D.a_init ? D.a_init : D.a0) : nullptr;
   int left = 0;
-  const double part = cluster_integrate<CL>(kc, D, init, D.n_steps, D.k0, q, sub, own, true, left);
+  const double part = cluster_integrate<CL, FULL>(kc, D, init, D.n_steps, D.k0, q, sub, own,
+                                                  true, left);
   const double s = cluster_sum<CL>(cta_sum(part, sm.red), sm, 0, q);
   if (threadIdx.x == 0 && q == 0)
     D.qoi_out[0] = (kc.qoi_kind == MQS_QOI_JOULE ? s / D.dt : 0.5 * s) * D.qoi_scale;
@@ -811,14 +826,14 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_propagate(const DirectLane* 
 
 // Parareal coarse sweep (Eq. 12), one cluster per sample; slice states
 // lane-major U/E/G[(sample*M + s) * n + i].
-template <int CL>
+template <int CL, bool FULL>
 __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __restrict__ lanes,
                                                         DirectConst kc, DirectChain ch) {
   __shared__ CSmem<CL> sm;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   double* own_w = reinterpret_cast<double*>(dyn_smem);
   const int ring_rows = cluster_ring_rows(kc.bw);
-  double* ring = own_w + own_rows<CL>(kc.n);
+  double* ring = FULL ? own_w : own_w + own_rows<CL>(kc.n);
   const unsigned q = CL > 1 ? cluster_rank() : 0u;
   const DirectLane D = lanes[blockIdx.x / CL];
   const int n = kc.n;
@@ -826,15 +841,15 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
   const int n_own = own.count();
   const int sample = D.sample;
   cluster_setup<CL>(sm);
-  Subst<CL> sub(D, own_w, ring, ring_rows, sm, n, kc.bw, (int)q);
+  Subst<CL, FULL> sub(D, own_w, ring, ring_rows, sm, n, kc.bw, (int)q);
   sub.stall = kc.stall_test != 0;
   const int s_stop = min(ch.s_end, ch.M - 1);
   for (int s = ch.s_begin; s < s_stop; ++s) {
     const int64_t base = ((int64_t)sample * ch.M + s) * n;
     const double* U0 = s == ch.s_first ? ch.U_prev : ch.U_cur;
     int left = 0;
-    cluster_integrate<CL>(kc, D, U0 + base, ch.steps_per_slice,
-                          (int64_t)s * ch.steps_per_slice, q, sub, own_w, false, left);
+    cluster_integrate<CL, FULL>(kc, D, U0 + base, ch.steps_per_slice,
+                                (int64_t)s * ch.steps_per_slice, q, sub, own_w, false, left);
     if (left) break;   // every CTA of the cluster leaves at the same slice
     double j2 = 0.0, u2 = 0.0;
     for (int idx = threadIdx.x; idx < n_own; idx += kNT) {
@@ -1093,16 +1108,17 @@ __global__ void __launch_bounds__(kNT, 1) k_band_chol_cl(double* __restrict__ LB
 }
 
 // ---------------------------------------------------------------- launch helpers
-template <int CL>
-const void* propagate_fn() { return reinterpret_cast<const void*>(&k_cluster_propagate<CL>); }
-template <int CL>
-const void* chain_fn() { return reinterpret_cast<const void*>(&k_cluster_chain<CL>); }
+template <int CL, bool FULL>
+const void* propagate_fn() { return reinterpret_cast<const void*>(&k_cluster_propagate<CL, FULL>); }
+template <int CL, bool FULL>
+const void* chain_fn() { return reinterpret_cast<const void*>(&k_cluster_chain<CL, FULL>); }
 
 template <int CL>
 size_t cluster_smem_t(int n, int bw) {
   return (size_t)(own_rows<CL>(n) + cluster_ring_rows(bw)) * sizeof(double);
 }
-size_t cluster_smem(int n, int bw, int CL) {
+// Shared memory of the own-rows + ring layout.
+size_t cluster_ring_smem(int n, int bw, int CL) {
   switch (CL) {
     case 1: return cluster_smem_t<1>(n, bw);
     case 2: return cluster_smem_t<2>(n, bw);
@@ -1110,19 +1126,38 @@ size_t cluster_smem(int n, int bw, int CL) {
     default: return cluster_smem_t<8>(n, bw);
   }
 }
+size_t fixed_smem(int CL) {
+  switch (CL) {
+    case 1: return sizeof(CSmem<1>);
+    case 2: return sizeof(CSmem<2>);
+    case 4: return sizeof(CSmem<4>);
+    default: return sizeof(CSmem<8>);
+  }
+}
+// The full work vector fits next to the static shared memory; env
+// MQS_CLUSTER_RING=1 takes the own-rows + ring layout anyway (for tests: both
+// layouts give bitwise the same results).
+bool cluster_full(int n, int CL) {
+  const char* v = getenv("MQS_CLUSTER_RING");
+  const bool force_ring = v && *v && atoi(v) != 0;
+  return !force_ring && (size_t)n * sizeof(double) + fixed_smem(CL) + 1024 <= 227 * 1024;
+}
+size_t cluster_smem(int n, int bw, int CL) {
+  return cluster_full(n, CL) ? (size_t)n * sizeof(double) : cluster_ring_smem(n, bw, CL);
+}
 
-template <int CL>
+template <int CL, bool FULL>
 int set_attrs(size_t smem) {
-  MQS_CUDA_TRY(cudaFuncSetAttribute(propagate_fn<CL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  MQS_CUDA_TRY(cudaFuncSetAttribute(chain_fn<CL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  MQS_CUDA_TRY(cudaFuncSetAttribute(propagate_fn<CL, FULL>(),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MQS_CUDA_TRY(cudaFuncSetAttribute(chain_fn<CL, FULL>(),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return MQS_OK;
 }
 
-template <int CL, class... Args>
+template <int CL, bool FULL, class... Args>
 int launch_cl(const void* fn, int n_lanes, size_t smem, cudaStream_t st, Args... args) {
-  MQS_TRY(set_attrs<CL>(smem));
+  MQS_TRY((set_attrs<CL, FULL>(smem)));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_lanes * CL));
   cfg.blockDim = dim3(kNT);
@@ -1141,9 +1176,9 @@ int launch_cl(const void* fn, int n_lanes, size_t smem, cudaStream_t st, Args...
   return MQS_OK;
 }
 
-template <int CL>
+template <int CL, bool FULL>
 int max_active_t(size_t smem) {
-  if (set_attrs<CL>(smem) != MQS_OK) return 0;
+  if (set_attrs<CL, FULL>(smem) != MQS_OK) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)CL);
   cfg.blockDim = dim3(kNT);
@@ -1156,7 +1191,7 @@ int max_active_t(size_t smem) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaOccupancyMaxActiveClusters(&nc, propagate_fn<CL>(), &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&nc, propagate_fn<CL, FULL>(), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1165,15 +1200,10 @@ int max_active_t(size_t smem) {
 
 }  // namespace
 
-// The own rows and the ring fit next to the static shared memory (227 KB per CTA).
+// The work vector (full copy, or own rows and the ring) fits next to the static
+// shared memory (227 KB per CTA).
 bool cluster_fits(int n, int bw, int CL) {
-  size_t fixed = sizeof(CSmem<8>);
-  switch (CL) {
-    case 1: fixed = sizeof(CSmem<1>); break;
-    case 2: fixed = sizeof(CSmem<2>); break;
-    case 4: fixed = sizeof(CSmem<4>); break;
-  }
-  return cluster_smem(n, bw, CL) + fixed + 1024 <= 227 * 1024;
+  return cluster_smem(n, bw, CL) + fixed_smem(CL) + 1024 <= 227 * 1024;
 }
 
 int cluster_max_active(int CL, int n, int bw) {
@@ -1184,16 +1214,17 @@ int cluster_max_active(int CL, int n, int bw) {
   if (slot < 0 || !cluster_fits(n, bw, CL)) return 0;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int64_t key = (int64_t)n * 65536 + bw;
+  const bool full = cluster_full(n, CL);
+  const int64_t key = ((int64_t)n * 65536 + bw) * 2 + (full ? 1 : 0);
   std::lock_guard<std::mutex> lk(mu);
   if (cache_n[slot] == key && cache[slot][0] == dev) return cache[slot][1];
   const size_t smem = cluster_smem(n, bw, CL);
   int r = 0;
   switch (CL) {
-    case 1: r = max_active_t<1>(smem); break;
-    case 2: r = max_active_t<2>(smem); break;
-    case 4: r = max_active_t<4>(smem); break;
-    case 8: r = max_active_t<8>(smem); break;
+    case 1: r = full ? max_active_t<1, true>(smem) : max_active_t<1, false>(smem); break;
+    case 2: r = full ? max_active_t<2, true>(smem) : max_active_t<2, false>(smem); break;
+    case 4: r = full ? max_active_t<4, true>(smem) : max_active_t<4, false>(smem); break;
+    case 8: r = full ? max_active_t<8, true>(smem) : max_active_t<8, false>(smem); break;
   }
   cache_n[slot] = key;
   cache[slot][0] = dev;
@@ -1249,14 +1280,27 @@ int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double*
   return MQS_OK;
 }
 
+namespace {
+template <int CL, class... Args>
+int launch_layout(bool chain, bool full, int n_lanes, size_t smem, cudaStream_t st,
+                  Args... args) {
+  if (full)
+    return launch_cl<CL, true>(chain ? chain_fn<CL, true>() : propagate_fn<CL, true>(), n_lanes,
+                               smem, st, args...);
+  return launch_cl<CL, false>(chain ? chain_fn<CL, false>() : propagate_fn<CL, false>(), n_lanes,
+                              smem, st, args...);
+}
+}  // namespace
+
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
   const size_t smem = cluster_smem(kc.n, kc.bw, kc.cluster);
+  const bool full = cluster_full(kc.n, kc.cluster);
   switch (kc.cluster) {
-    case 1: return launch_cl<1>(propagate_fn<1>(), n_lanes, smem, st, d_lanes, kc);
-    case 2: return launch_cl<2>(propagate_fn<2>(), n_lanes, smem, st, d_lanes, kc);
-    case 4: return launch_cl<4>(propagate_fn<4>(), n_lanes, smem, st, d_lanes, kc);
-    case 8: return launch_cl<8>(propagate_fn<8>(), n_lanes, smem, st, d_lanes, kc);
+    case 1: return launch_layout<1>(false, full, n_lanes, smem, st, d_lanes, kc);
+    case 2: return launch_layout<2>(false, full, n_lanes, smem, st, d_lanes, kc);
+    case 4: return launch_layout<4>(false, full, n_lanes, smem, st, d_lanes, kc);
+    case 8: return launch_layout<8>(false, full, n_lanes, smem, st, d_lanes, kc);
   }
   set_error("unsupported cluster size %d", kc.cluster);
   return MQS_EINVAL;
@@ -1266,11 +1310,12 @@ int launch_cluster_chain(const DirectLane* d_lanes, int n_lanes, const DirectCon
                          const DirectChain& ch, cudaStream_t st) {
   if (n_lanes <= 0) return MQS_OK;
   const size_t smem = cluster_smem(kc.n, kc.bw, kc.cluster);
+  const bool full = cluster_full(kc.n, kc.cluster);
   switch (kc.cluster) {
-    case 1: return launch_cl<1>(chain_fn<1>(), n_lanes, smem, st, d_lanes, kc, ch);
-    case 2: return launch_cl<2>(chain_fn<2>(), n_lanes, smem, st, d_lanes, kc, ch);
-    case 4: return launch_cl<4>(chain_fn<4>(), n_lanes, smem, st, d_lanes, kc, ch);
-    case 8: return launch_cl<8>(chain_fn<8>(), n_lanes, smem, st, d_lanes, kc, ch);
+    case 1: return launch_layout<1>(true, full, n_lanes, smem, st, d_lanes, kc, ch);
+    case 2: return launch_layout<2>(true, full, n_lanes, smem, st, d_lanes, kc, ch);
+    case 4: return launch_layout<4>(true, full, n_lanes, smem, st, d_lanes, kc, ch);
+    case 8: return launch_layout<8>(true, full, n_lanes, smem, st, d_lanes, kc, ch);
   }
   set_error("unsupported cluster size %d", kc.cluster);
   return MQS_EINVAL;

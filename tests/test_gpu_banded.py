@@ -497,3 +497,43 @@ def test_pipelined_parareal_iteration_limit(ctx, mqs):
         q_ref = stepper.qoi_finish(stepper.QOI_JOULE, ref["qoi_raw"], n_steps, dt)
         assert abs(q[0, 0] - q_ref) <= TOL * abs(q_ref)
         assert _rel(ctx.read_state(b, 0)[0], ref["a_end"]) <= TOL
+
+
+@pytest.mark.parametrize("cl", [1, 2, 4, 8])
+def test_cluster_layouts_are_bitwise_equal(ctx, mqs, monkeypatch, cl):
+    """The cluster stepping kernels keep either a full copy of the work vector
+    (meshes that fit shared memory) or their own rows plus a ring of recently
+    solved rows; the arithmetic and its order are the same, so both layouts
+    give bitwise the same QoI, final states and Parareal iterations on every
+    cluster size."""
+    mesh = meshes.annulus("5k")
+    p = params.annulus_samples(3, 0, seed=71 + cl)
+    n_steps = 96
+    dt = configs.PERIOD / 128
+    mid = ctx.upload_mesh(mesh)
+    monkeypatch.setenv("MQS_DIRECT_CLUSTER", str(cl))
+    monkeypatch.setenv("MQS_CHAIN_CLUSTER", str(cl))
+    out = []
+    for ring in ("0", "1"):
+        monkeypatch.setenv("MQS_CLUSTER_RING", ring)
+        b = ctx.set_samples(mid, p)
+        ctx.set_solver(b, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+        ctx.propagate(b, 0, dt)
+        q, st = ctx.read_qoi(b)
+        assert not st.any()
+        b2 = ctx.set_samples(mid, p[:1])
+        ctx.set_solver(b2, mqs.MQS_SOLVER_BANDED)
+        ctx.set_time(b2, 0.0, n_steps * dt, 50.0, mqs.MQS_QOI_JOULE)
+        K = ctx.propagate(b2, 0, dt, n_slices=12, coarse_factor=4, max_par_iters=12,
+                          par_tol=1e-8)
+        q2, st2 = ctx.read_qoi(b2)
+        assert not st2.any()
+        out.append((q.copy(), ctx.read_state(b, 0), K, q2.copy(), ctx.read_state(b2, 0)))
+    full, ring = out
+    assert np.array_equal(full[0], ring[0]) and np.array_equal(full[1], ring[1])
+    assert full[2] == ring[2]
+    assert np.array_equal(full[3], ring[3]) and np.array_equal(full[4], ring[4])
+    q_ref, a_ref, _ = stepper.solve_sample(mesh, p[0], dt, n_steps, stepper.QOI_JOULE)
+    assert abs(full[0][0, 0] - q_ref) <= TOL * abs(q_ref)
+    assert _rel(full[1][0], a_ref) <= TOL
