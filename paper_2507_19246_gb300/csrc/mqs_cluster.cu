@@ -472,13 +472,12 @@ struct Subst {
 
   // pre of round g1 (lane partial over its own rows): B s - C2 y_{b-2}
   // (forward) or B^T s - D2^T u_{b+2} (backward); the first backward round
-  // takes s = y_b (no band part, no couplings).
-  __device__ double pre_of(int g1, const double (&pf)[kPF]) const {
+  // takes s = y_b (no band part, no couplings).  The B s part needs only s
+  // (ready a round before y_{b-2}), so it is taken before the wait for y.
+  __device__ double pre_bs(int g1, const double (&pf)[kPF]) const {
     const int b1 = block_of(g1);
-    double p0 = 0.0, p1 = 0.0;
+    double p0 = 0.0;
     const bool first_bwd = g1 == nblk;
-    const bool two = g1 < nblk ? b1 >= 2 : g1 >= nblk + 2;
-    const int bb = block_of(g1 - 2);
     const double* s1 = sm.s[g1 & 3];
 #pragma unroll
     for (int k = 0; k < S::TPP; ++k) {
@@ -486,13 +485,23 @@ struct Subst {
       double bv;
       if constexpr (S::PF_B) bv = pf[k]; else bv = b_val(g1, t);
       p0 = fma(bv, first_bwd ? own_val(b1, t) : s1[t], p0);
-      if (two) {
-        double c2;
-        if constexpr (S::PF_C2) c2 = pf[S::TPP + k]; else c2 = c2_val(g1, t);
-        p1 = fma(-c2, own_val(bb, t), p1);
-      }
     }
-    return p0 + p1;
+    return p0;
+  }
+  __device__ double pre_c2(int g1, const double (&pf)[kPF]) const {
+    const int b1 = block_of(g1);
+    double p1 = 0.0;
+    const bool two = g1 < nblk ? b1 >= 2 : g1 >= nblk + 2;
+    if (!two) return p1;
+    const int bb = block_of(g1 - 2);
+#pragma unroll
+    for (int k = 0; k < S::TPP; ++k) {
+      const int t = p_g + S::LPRP * k;
+      double c2;
+      if constexpr (S::PF_C2) c2 = pf[S::TPP + k]; else c2 = c2_val(g1, t);
+      p1 = fma(-c2, own_val(bb, t), p1);
+    }
+    return p1;
   }
 
   // Forward then backward substitution; on return w holds u (all rows).
@@ -540,13 +549,13 @@ struct Subst {
       // pre of every round, one round ahead of the exchange warps
       for (int g1 = 0; g1 < G; ++g1) {
         p_load(g1, pf);
-        if (g1 == nblk) {
+        if (g1 == nblk)
           wait_count(&sm.ydone, nblk, &sm.err);          // y of the last forward block
-        } else {
-          wait_count(&sm.ydone, g1 - 1, &sm.err);        // the block two rounds back
+        else
           wait_count(&sm.sdone, g1, &sm.err);
-        }
-        const double v = row_sum<S::RWP>(pre_of(g1, pf));
+        const double p0 = pre_bs(g1, pf);
+        if (g1 != nblk) wait_count(&sm.ydone, g1 - 1, &sm.err);   // the block two rounds back
+        const double v = row_sum<S::RWP>(p0 + pre_c2(g1, pf));
         if (p_g == 0) sm.pre[g1 & 1][p_r] = v;
         group_sync(3, S::NP * 32);
         if (threadIdx.x == S::P0 * 32) st_release(&sm.pdone, g1);
