@@ -105,6 +105,7 @@ struct CSmem {
   int ydone;                                 // rounds whose solved block is in the copy
   int sdone;                                 // rounds whose s is in the ring
   int pdone;                                 // rounds whose pre is in shared memory
+  int ccount;                                // exchange warps done with their C1 product
   int err;                                   // a wait ran out
   int flag_pub[2];                           // step-boundary snapshot: 1 error, 2 cancelled
   double red[kNW];
@@ -411,25 +412,34 @@ struct Subst {
         acc0 = fma(__ldg(LB + cur.off + k * cur.step), ring_at(cur.w0 + k * cur.wstep), acc0);
     cur = gemv_desc(j + 1);
     gemv_load(cur, pf);
-    double acc = acc0 + acc1;
+    // a warp without band terms (most rounds of a narrow band) skips its
+    // reduction: s = own value exactly, as own - 0 would give
     double* sj = sm.s[j & 3];
     if (j < nblk) {
-      acc += __shfl_xor_sync(kFull, acc, 1);
-      acc += __shfl_xor_sync(kFull, acc, 2);
-      if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 4);
-      if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 8);
-      if (S::H > 4) acc += __shfl_xor_sync(kFull, acc, 16);
+      double acc = 0.0;
+      if (cmax > 0) {
+        acc = acc0 + acc1;
+        acc += __shfl_xor_sync(kFull, acc, 1);
+        acc += __shfl_xor_sync(kFull, acc, 2);
+        if (S::H > 1) acc += __shfl_xor_sync(kFull, acc, 4);
+        if (S::H > 2) acc += __shfl_xor_sync(kFull, acc, 8);
+        if (S::H > 4) acc += __shfl_xor_sync(kFull, acc, 16);
+      }
       if (f_g == 0 && f_h == 0) {
         const int row = j * kB + q * S::R + f_t;
-        sj[f_t] = row < n ? own_at(j, f_t) - acc : 0.0;
+        sj[f_t] = row < n ? (cmax > 0 ? own_at(j, f_t) - acc : own_at(j, f_t)) : 0.0;
       }
     } else {
+      double acc = 0.0;
+      if (cmax > 0) {
+        acc = acc0 + acc1;
 #pragma unroll
-      for (int o = S::TB; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        for (int o = S::TB; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      }
       if (b_kg == 0) {
         const int bt = 2 * nblk - 1 - j;
         const int row = bt * kB + q * S::R + b_t;
-        sj[b_t] = row < n ? own_at(bt, b_t) - acc : 0.0;
+        sj[b_t] = row < n ? (cmax > 0 ? own_at(bt, b_t) - acc : own_at(bt, b_t)) : 0.0;
       }
     }
   }
@@ -488,9 +498,10 @@ struct Subst {
     }
     return p0;
   }
-  __device__ double pre_c2(int g1, const double (&pf)[kPF]) const {
+  // continues the B s partial p with the C2 term
+  __device__ double pre_c2(int g1, const double (&pf)[kPF], double p) const {
     const int b1 = block_of(g1);
-    double p1 = 0.0;
+    double p1 = p;
     const bool two = g1 < nblk ? b1 >= 2 : g1 >= nblk + 2;
     if (!two) return p1;
     const int bb = block_of(g1 - 2);
@@ -511,6 +522,7 @@ struct Subst {
       sm.ydone = -1;
       sm.sdone = -1;
       sm.pdone = -1;
+      sm.ccount = 0;
     }
     __syncthreads();
     if (is_gemv()) {
@@ -555,7 +567,11 @@ struct Subst {
           wait_count(&sm.sdone, g1, &sm.err);
         const double p0 = pre_bs(g1, pf);
         if (g1 != nblk) wait_count(&sm.ydone, g1 - 1, &sm.err);   // the block two rounds back
-        const double v = row_sum<S::RWP>(p0 + pre_c2(g1, pf));
+        // the C2 term waits until every exchange warp has its C1 product of
+        // the previous round: that product is on the critical path, this one
+        // has the share exchange's latency as slack
+        if (g1 >= 2 && g1 != nblk) wait_count(&sm.ccount, S::NX * g1, &sm.err);
+        const double v = row_sum<S::RWP>(pre_c2(g1, pf, p0));
         if (p_g == 0) sm.pre[g1 & 1][p_r] = v;
         group_sync(3, S::NP * 32);
         if (threadIdx.x == S::P0 * 32) st_release(&sm.pdone, g1);
@@ -609,6 +625,8 @@ struct Subst {
           }
         }
         const double v = row_sum<S::RW>(v0 + v1);
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sm.ccount, 1);
         if constexpr (CL == 1) {
           const int row = b * kB + x_r;
           if (x_g == 0 && row < n) put_solved(row, v);
