@@ -471,12 +471,19 @@ struct Subst {
         pf[k] = g < 2 * nblk ? c1_val(g, x_g + S::LPR * k) : 0.0;
     }
   }
-  __device__ void p_load(int g1, double (&pf)[kPF]) const {
+  // pre operands of round g1 into registers: B into pf[0, TPP), C2 into
+  // pf[TPP, 2 TPP) (each only where it fits)
+  __device__ void p_load_b(int g1, double (&pf)[kPF]) const {
+    if constexpr (S::PF_B) {
 #pragma unroll
-    for (int k = 0; k < S::TPP; ++k) {
-      const int t = p_g + S::LPRP * k;
-      if constexpr (S::PF_B) pf[k] = g1 < 2 * nblk ? b_val(g1, t) : 0.0;
-      if constexpr (S::PF_C2) pf[S::TPP + k] = g1 < 2 * nblk ? c2_val(g1, t) : 0.0;
+      for (int k = 0; k < S::TPP; ++k) pf[k] = g1 < 2 * nblk ? b_val(g1, p_g + S::LPRP * k) : 0.0;
+    }
+  }
+  __device__ void p_load_c2(int g1, double (&pf)[kPF]) const {
+    if constexpr (S::PF_C2) {
+#pragma unroll
+      for (int k = 0; k < S::TPP; ++k)
+        pf[S::TPP + k] = g1 < 2 * nblk ? c2_val(g1, p_g + S::LPRP * k) : 0.0;
     }
   }
 
@@ -558,14 +565,24 @@ struct Subst {
         if (gt == 0) st_release(&sm.sdone, j);
       }
     } else if (is_pre()) {
-      // pre of every round, one round ahead of the exchange warps
-      for (int g1 = 0; g1 < G; ++g1) {
-        p_load(g1, pf);
+      // pre of every round, one round ahead of the exchange warps, software
+      // pipelined: round g1 + 1's B values load while round g1 waits for its
+      // C2 operands and its C2 values once round g1's C2 term is formed; its
+      // B s part follows the release of round g1, while the exchange warps
+      // wait for shares, so that the FP64 pipe is free for their C1 product
+      // when the solved block arrives.
+      auto bs_of = [&](int g1) -> double {
         if (g1 == nblk)
           wait_count(&sm.ydone, nblk, &sm.err);          // y of the last forward block
         else
           wait_count(&sm.sdone, g1, &sm.err);
-        const double p0 = pre_bs(g1, pf);
+        return pre_bs(g1, pf);
+      };
+      p_load_b(0, pf);
+      p_load_c2(0, pf);
+      double p0 = bs_of(0);
+      for (int g1 = 0; g1 < G; ++g1) {
+        if (g1 + 1 < G) p_load_b(g1 + 1, pf);
         if (g1 != nblk) wait_count(&sm.ydone, g1 - 1, &sm.err);   // the block two rounds back
         // the C2 term waits until every exchange warp has its C1 product of
         // the previous round: that product is on the critical path, this one
@@ -575,6 +592,10 @@ struct Subst {
         if (p_g == 0) sm.pre[g1 & 1][p_r] = v;
         group_sync(3, S::NP * 32);
         if (threadIdx.x == S::P0 * 32) st_release(&sm.pdone, g1);
+        if (g1 + 1 < G) {
+          p_load_c2(g1 + 1, pf);
+          p0 = bs_of(g1 + 1);
+        }
       }
     } else if (is_exch()) {
       x_load(0, pf);
