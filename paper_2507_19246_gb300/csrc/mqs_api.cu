@@ -43,7 +43,7 @@ struct FactorSet {
   double dt = 0.0;
   bool have64 = false, have32 = false, have_cpl = false;
   DevBuf LB, invd, Binv, bad;   // [samples][n][bw+1], [samples][n], [samples][n/32][32][32], [samples]
-  DevBuf B64, C1, C2, D1, D2;   // [samples][n/64][64][64] block inverses and couplings (cluster kernels)
+  DevBuf B64, B64T, C1, C2, D1, D2;   // [samples][n/64][64][64] block inverses and couplings (cluster kernels)
   DevBuf LBf, invdf, Binvf;     // FP32 factor (mixed precision)
 };
 
@@ -709,10 +709,11 @@ size_t cluster_bstride(const MeshDev& m) {
 int ensure_couplings(mqs_ctx* ctx, Batch& b, const MeshDev& m, FactorSet& f) {
   if (f.have_cpl) return MQS_OK;
   const size_t bstride = cluster_bstride(m);
-  for (DevBuf* x : {&f.B64, &f.C1, &f.C2, &f.D1, &f.D2})
+  for (DevBuf* x : {&f.B64, &f.B64T, &f.C1, &f.C2, &f.D1, &f.D2})
     MQS_TRY(x->ensure(bstride * b.n * sizeof(double)));
-  MQS_TRY(block_prep(m, b.n, f.LB.as<double>(), f.B64.as<double>(), f.C1.as<double>(),
-                     f.C2.as<double>(), f.D1.as<double>(), f.D2.as<double>(), ctx->c.stream));
+  MQS_TRY(block_prep(m, b.n, f.LB.as<double>(), f.B64.as<double>(), f.B64T.as<double>(),
+                     f.C1.as<double>(), f.C2.as<double>(), f.D1.as<double>(), f.D2.as<double>(),
+                     ctx->c.stream));
   f.have_cpl = true;
   return MQS_OK;
 }
@@ -789,6 +790,7 @@ DirectLane direct_lane(const MeshDev& m, const Batch& b, const FactorSet& f, int
   d.Binv = f.Binv.as<double>() + (size_t)block_count(m.n_free) * 32 * 32 * sample;
   const size_t bo = cluster_bstride(m) * sample;
   d.B64 = f.B64.as<double>() + bo;
+  d.B64T = f.B64T.as<double>() + bo;
   d.C1 = f.C1.as<double>() + bo;
   d.C2 = f.C2.as<double>() + bo;
   d.D1 = f.D1.as<double>() + bo;

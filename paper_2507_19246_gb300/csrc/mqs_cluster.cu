@@ -269,8 +269,9 @@ struct Subst {
   static constexpr int kBB = kB * kB;
   const double* __restrict__ LB;
   const double* __restrict__ B;    // 64 x 64 diagonal-block inverses [b][r][t]
-  const double* __restrict__ C1;   // [b][r][t]
-  const double* __restrict__ C2;   // [b][r][t]
+  const double* __restrict__ BT;   // B^T: [b][t][r]
+  const double* __restrict__ C1;   // [b][t][r]
+  const double* __restrict__ C2;   // [b][t][r]
   const double* __restrict__ D1;   // D1_b^T: [b][t][r]
   const double* __restrict__ D2;   // D2_b^T: [b][t][r]
   // work vector: this CTA's own rows of every block (own[b * R + t] = row
@@ -293,7 +294,7 @@ struct Subst {
 
   __device__ Subst(const DirectLane& D, double* own_, double* ring_, int ring_rows,
                    CSmem<CL>& sm_, int n_, int bw_, int q_)
-      : LB(D.LB), B(D.B64), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), own(own_), ring(ring_),
+      : LB(D.LB), B(D.B64), BT(D.B64T), C1(D.C1), C2(D.C2), D1(D.D1), D2(D.D2), own(own_), ring(ring_),
         ring_mask(ring_rows - 1), sm(sm_), n(n_), bw(bw_), W(bw_ + 1),
         nblk((n_ + kB - 1) / kB), q(q_) {
     warp = threadIdx.x >> 5;
@@ -449,18 +450,18 @@ struct Subst {
   __device__ double c1_val(int g, int t) const {
     const int b = block_of(g), tc = q * S::R + t;
     const int64_t o = (int64_t)b * kBB;
-    if (g < nblk) return b >= 1 ? __ldg(C1 + o + x_r * kB + tc) : 0.0;
+    if (g < nblk) return b >= 1 ? __ldg(C1 + o + tc * kB + x_r) : 0.0;
     return g >= nblk + 1 ? __ldg(D1 + o + tc * kB + x_r) : 0.0;
   }
   __device__ double b_val(int g1, int t) const {
     const int b1 = block_of(g1), tc = q * S::R + t;
     const int64_t o = (int64_t)b1 * kBB;
-    return g1 < nblk ? __ldg(B + o + p_r * kB + tc) : __ldg(B + o + tc * kB + p_r);
+    return g1 < nblk ? __ldg(BT + o + tc * kB + p_r) : __ldg(B + o + tc * kB + p_r);
   }
   __device__ double c2_val(int g1, int t) const {
     const int b1 = block_of(g1), tc = q * S::R + t;
     const int64_t o = (int64_t)b1 * kBB;
-    if (g1 < nblk) return b1 >= 2 ? __ldg(C2 + o + p_r * kB + tc) : 0.0;
+    if (g1 < nblk) return b1 >= 2 ? __ldg(C2 + o + tc * kB + p_r) : 0.0;
     return (g1 != nblk && g1 >= nblk + 2) ? __ldg(D2 + o + tc * kB + p_r) : 0.0;
   }
 
@@ -927,13 +928,18 @@ __global__ void __launch_bounds__(kNT, 1) k_cluster_chain(const DirectLane* __re
 // One CTA per (64-row block b, factor): the inverse B_b of the unit lower
 // diagonal block of L~ (identity rows past n) by forward substitution, one
 // thread per column, then the couplings as dense products: C1_b = B_b
-// L~_{b,b-1}, C2_b = B_b L~_{b,b-2} stored [r][t]; D1_b^T = L~_{b+1,b} B_b,
-// D2_b^T = L~_{b+2,b} B_b stored [t][r] (zero where the block is absent).
+// L~_{b,b-1}, C2_b = B_b L~_{b,b-2}; D1_b^T = L~_{b+1,b} B_b, D2_b^T =
+// L~_{b+2,b} B_b (zero where the block is absent).  Everything the forward
+// sweep reads (B_b, C1_b, C2_b) is stored column-major [t][r] and what the
+// backward sweep reads (B_b^T, D1_b^T, D2_b^T) as [t][r] of the transpose,
+// i.e. B_b row-major [r][t]: a lane of the stepping kernels takes one row r,
+// consecutive lanes consecutive rows, so every load of a warp is coalesced.
 constexpr int kPrepThreads = 256;
 
 __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __restrict__ LBall, int n,
                                                             int bw, int64_t fstride, int nblk,
                                                             double* __restrict__ B_all,
+                                                            double* __restrict__ BT_all,
                                                             double* __restrict__ C1_all,
                                                             double* __restrict__ C2_all,
                                                             double* __restrict__ D1_all,
@@ -966,7 +972,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __res
     }
   }
   __syncthreads();
-  for (int e = tid; e < kB * kB; e += kPrepThreads) B_all[bo + e] = Bs[e / kB][e % kB];
+  for (int e = tid; e < kB * kB; e += kPrepThreads) {
+    B_all[bo + e] = Bs[e / kB][e % kB];
+    BT_all[bo + e] = Bs[e % kB][e / kB];
+  }
   double* outs[4] = {C1_all, C2_all, D1_all, D2_all};
   for (int which = 0; which < 4; ++which) {
     __syncthreads();
@@ -979,7 +988,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_block_prep(const double* __res
     }
     __syncthreads();
     for (int e = tid; e < kB * kB; e += kPrepThreads) {
-      const int r = e / kB, c = e % kB;
+      // C1, C2 column-major: element (r, c) at [c][r]; D1^T, D2^T as computed
+      const int r = which < 2 ? e % kB : e / kB, c = which < 2 ? e / kB : e % kB;
       double a0 = 0.0, a1 = 0.0;
       if (which < 2) {
 #pragma unroll 8
@@ -1313,8 +1323,8 @@ int band_chol_cluster_size() { return 8; }
 // shared memory: bandwidths up to ~300 on 8 CTAs.
 bool band_chol_cluster_fits(int bw) { return CholRing<8>::bytes(bw) <= 200 * 1024; }
 
-int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
-               double* D1, double* D2, cudaStream_t st) {
+int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* BT, double* C1,
+               double* C2, double* D1, double* D2, cudaStream_t st) {
   const int nblk = (m.n_free + kB - 1) / kB;
   const int64_t fstride = (int64_t)m.n_free * (m.bw + 1);
   if (n_fac <= 0) return MQS_OK;
@@ -1322,7 +1332,7 @@ int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double*
   MQS_CUDA_TRY(cudaFuncSetAttribute(k_block_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   k_block_prep<<<dim3((unsigned)nblk, (unsigned)n_fac), kPrepThreads, smem, st>>>(
-      LB, m.n_free, m.bw, fstride, nblk, B, C1, C2, D1, D2);
+      LB, m.n_free, m.bw, fstride, nblk, B, BT, C1, C2, D1, D2);
   MQS_CUDA_TRY(cudaGetLastError());
   count_launch();
   return MQS_OK;

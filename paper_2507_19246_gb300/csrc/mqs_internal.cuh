@@ -162,9 +162,10 @@ struct DirectLane {
   const double* invd;      // its reciprocal diagonal [n]
   const double* Binv;      // inverses of its 32 x 32 unit diagonal blocks [n/32][32][32]
   // 64-row blocks of the cluster kernels, [ceil(n/64)][64][64] each:
-  const double* B64;       // inverse of the unit lower diagonal block
-  const double* C1;        // B_b L~_{b,b-1}   [b][r][t]
-  const double* C2;        // B_b L~_{b,b-2}   [b][r][t]
+  const double* B64;       // inverse of the unit lower diagonal block   [b][r][t]
+  const double* B64T;      // its transpose                              [b][t][r]
+  const double* C1;        // B_b L~_{b,b-1}   column-major [b][t][r]
+  const double* C2;        // B_b L~_{b,b-2}   column-major [b][t][r]
   const double* D1;        // L~_{b+1,b} B_b   [b][t][r]
   const double* D2;        // L~_{b+2,b} B_b   [b][t][r]
   const float* LBf;        // FP32 factor, reciprocal diagonal and block inverses (mixed)
@@ -247,8 +248,8 @@ int band_chol_cluster(double* LB, double* invd, int n, int bw, int64_t fstride, 
                       int32_t* bad, cudaStream_t st);
 int band_chol_cluster_size();
 bool band_chol_cluster_fits(int bw);
-int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* C1, double* C2,
-               double* D1, double* D2, cudaStream_t st);
+int block_prep(const MeshDev& m, int n_fac, const double* LB, double* B, double* BT, double* C1,
+               double* C2, double* D1, double* D2, cudaStream_t st);
 bool cluster_fits(int n, int bw, int CL);          // own rows + ring fit a CTA's shared memory
 int cluster_max_active(int CL, int n, int bw);      // resident clusters (0: does not fit)
 int launch_cluster(const DirectLane* d_lanes, int n_lanes, const DirectConst& kc, cudaStream_t st);
