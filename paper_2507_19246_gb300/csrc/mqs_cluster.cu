@@ -647,6 +647,10 @@ struct Subst {
           }
         }
         const double v = row_sum<S::RW>(v0 + v1);
+        // next round's C1 values; with 4 and 8 CTAs (3 and 7 remote stores
+        // per lane) before the shares, so that these loads do not queue
+        // behind the stores -- measured faster there, slower with 2 CTAs
+        if constexpr (CL >= 4) x_load(g + 1, pf);
         __syncwarp();
         if ((threadIdx.x & 31) == 0) atomicAdd(&sm.ccount, 1);
         if constexpr (CL == 1) {
@@ -666,7 +670,7 @@ struct Subst {
               st_async(map_rank(la, p), v, map_rank(lm, p));
           }
         }
-        x_load(g + 1, pf);
+        if constexpr (CL < 4) x_load(g + 1, pf);
       }
     }
     __syncthreads();
