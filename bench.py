@@ -889,8 +889,11 @@ def run_mlmc(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5; 1 for mlmcpar80k, whose step is a whole "
+                    "MLMC estimate of several minutes)")
+    ap.add_argument("--warmup", type=int, default=None,
+                    help="untimed warm-up steps (default 3; 1 for mlmcpar80k)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="parareal20k",
@@ -903,6 +906,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the GPU serial solve and the MLMC FP64/mixed records")
     args = ap.parse_args()
+    long_step = args.workload == "mlmcpar80k"
+    if args.steps is None:
+        args.steps = 1 if long_step else 5
+    if args.warmup is None:
+        args.warmup = 1 if long_step else 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
