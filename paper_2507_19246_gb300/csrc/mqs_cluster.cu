@@ -492,13 +492,25 @@ struct Subst {
   // (forward) or B^T s - D2^T u_{b+2} (backward); the first backward round
   // takes s = y_b (no band part, no couplings).  The B s part needs only s
   // (ready a round before y_{b-2}), so it is taken before the wait for y.
+  // B_b is lower triangular (exact zeros above the diagonal): a warp skips
+  // the column groups k whose every column lies above its rows (forward, B
+  // s) or below them (backward, B^T s) -- products that are exactly zero.
   __device__ double pre_bs(int g1, const double (&pf)[kPF]) const {
     const int b1 = block_of(g1);
     double p0 = 0.0;
     const bool first_bwd = g1 == nblk;
     const double* s1 = sm.s[g1 & 3];
+    const int r0 = (warp - S::P0) * S::RWP, r1 = r0 + S::RWP - 1;   // the warp's rows
+    const int c0 = q * S::R;                                          // first own column
+    // forward: group k is nonzero while c0 + LPRP k <= r1; backward while
+    // c0 + LPRP k + LPRP - 1 >= r0
+    const int k_end = g1 < nblk ? (r1 - c0 < 0 ? 0 : (r1 - c0) / S::LPRP + 1) : S::TPP;
+    const int k_begin = g1 < nblk ? 0 : (r0 - c0 - S::LPRP + 1 <= 0 ? 0
+                                          : (r0 - c0 - S::LPRP + 1 + S::LPRP - 1) / S::LPRP);
 #pragma unroll
     for (int k = 0; k < S::TPP; ++k) {
+      if (k >= k_end) break;
+      if (k < k_begin) continue;
       const int t = p_g + S::LPRP * k;
       double bv;
       if constexpr (S::PF_B) bv = pf[k]; else bv = b_val(g1, t);
