@@ -18,23 +18,27 @@
 //   backward L~^T u = y:  u_b = B_b^T (y_b - Q_b) - D1_b u_{b+1} - D2_b u_{b+2},
 //                         D1_b = B_b^T L~_{b+1,b}^T, D2_b = B_b^T L~_{b+2,b}^T,
 //                         Q_b = sum_{k >= b+3} L~_kb^T u_k
-// The couplings are precomputed with the factor.  Warp roles: GEMV warps form
-// s_b = w_b - P_b (or y_b - Q_b) for the block solved two rounds later; pre
-// warps form pre_b = B_b s_b - C2_b y_{b-2} one round ahead; exchange warps
-// (alone on their SM sub-partitions) gather the last block, form
+// The couplings are precomputed with the factor, laid out so that every warp
+// load is coalesced.  Warp roles: GEMV warps form s_b = w_b - P_b (or y_b -
+// Q_b) for the block solved two rounds later; pre warps form pre_b = B_b s_b -
+// C2_b y_{b-2} one round ahead (B_b s_b as soon as s_b is ready, the C2 term
+// once the exchange warps have their C1 products, skipping the zero products
+// of the triangular B_b); exchange warps gather the last block, form
 // v_b = pre_b - C1_b y_{b-1} and send it, which is the whole critical path of
-// a round.  The warp groups hand data over through release/acquire progress
-// counters in shared memory, never through a CTA-wide barrier.
+// a round, kept as far as possible alone on the FP64 pipe.  The warp groups
+// hand data over through release/acquire progress counters in shared memory,
+// never through a CTA-wide barrier.
 //
-// Cluster split: every CTA keeps a full copy of the permuted work vector in
-// shared memory and owns rows q*R .. q*R+R-1 (R = 64/CL) of every block, in
+// Cluster split: every CTA keeps the permuted work vector in shared memory --
+// a full copy where it fits, otherwise its own rows and a ring of recently
+// solved rows -- and owns rows q*R .. q*R+R-1 (R = 64/CL) of every block, in
 // the band ordering.  Per block it computes s for its own rows and its share
 // of the block solve, v_q = pre_q - C1_b[:, own] y_{b-1}[own], which it sends
 // to every CTA of the cluster with asynchronous DSMEM stores that complete on
 // the receiver's mbarrier (no fence on the sending side, no cluster barrier
-// per block); each CTA adds the CL shares in rank order, so all copies hold
-// identical values.  Waits are bounded: a wait that runs out sets
-// MQS_ST_TIMEOUT on the lane and the kernel skips every later wait.
+// per block); each CTA adds the CL shares in rank order, so all copies (full
+// or ring) hold identical values.  Waits are bounded: a wait that runs out
+// sets MQS_ST_TIMEOUT on the lane and the kernel skips every later wait.
 // Node-wise work (right-hand side, y = M a, QoI) is split by the same row
 // ownership, so a step exchanges no data through global memory except the new
 // state a1, which is published by a cluster barrier before y = M a1.
