@@ -158,3 +158,86 @@ def test_three_phase_currents_by_hand():
     # r(t) = sum_p J_p(t) F_p: at t = 1/600 s only phases 0 and 2 contribute
     r = d.source(1.0 / 600.0)
     assert np.allclose(r, 2.0 * d.F[0] - 2.2 * d.F[2], rtol=1e-14, atol=1e-14 * np.abs(r).max())
+
+
+# ---------------------------------------------------------------- annulus closed forms
+# On the annulus meshes with one material everywhere, the continuous problem
+# behind Eq. 2-5 (Sec. II-A) is radially symmetric and has closed forms: the
+# steady state of a uniform current density, and the slowest decaying mode.
+# The oracle's P1 matrices must reach both at second order in the mesh size
+# (nodes lie on the circles; the 80k mesh halves both spacings of the 20k one).
+R_IN, R_OUT = 0.02, 0.10
+NU_ANN = 1.0 / (4e-7 * np.pi * 100.0)        # a relative permeability of 100
+SIGMA_ANN, J_ANN = 3.0e7, 1.0e6
+
+
+def _uniform_annulus(kind, sigma, j0, all_source):
+    from dataclasses import replace
+    m = meshes.annulus(kind)
+    kw = {"region": np.zeros_like(m.region)}
+    if all_source:
+        kw.update(src_phase=np.zeros_like(m.src_phase), src_coef=np.ones_like(m.src_coef))
+    mm = replace(m, **kw)
+    r, p = mm.n_regions, mm.n_phases
+    prm = np.concatenate([np.full(r, sigma), np.full(r, NU_ANN), [j0],
+                          [1.0] + [0.0] * (p - 1), [0.0] * p])
+    return mm, fem.Discretisation(mm, prm)
+
+
+def _steady_errors(kind):
+    """-nu (1/r)(r A')' = J, A(R_IN) = A(R_OUT) = 0:
+    A = -J r^2/(4 nu) + c1 ln r + c2."""
+    import scipy.sparse.linalg as spla
+    from scipy.integrate import quad
+    c1 = J_ANN * (R_OUT ** 2 - R_IN ** 2) / (4 * NU_ANN * np.log(R_OUT / R_IN))
+    c2 = J_ANN * R_IN ** 2 / (4 * NU_ANN) - c1 * np.log(R_IN)
+    exact = lambda r: -J_ANN * r ** 2 / (4 * NU_ANN) + c1 * np.log(r) + c2
+    dexact = lambda r: -J_ANN * r / (2 * NU_ANN) + c1 / r
+    energy = 0.5 * quad(lambda r: NU_ANN * dexact(r) ** 2 * 2 * np.pi * r, R_IN, R_OUT,
+                        limit=200, epsabs=0.0, epsrel=1e-13)[0]
+    mm, d = _uniform_annulus(kind, 1.0, J_ANN, True)
+    a = spla.spsolve(d.K.tocsc(), J_ANN * d.F[0])
+    r = np.hypot(*mm.xy[d.free].T)
+    nodal = np.max(np.abs(a - exact(r))) / np.max(np.abs(exact(r)))
+    return nodal, (0.5 * a @ (d.K @ a) - energy) / energy
+
+
+def test_annulus_steady_state_matches_the_radial_closed_form():
+    """K and F (Eq. 4-5) on the annulus against the closed-form steady state
+    of a uniform current density: nodal error and energy converge at second
+    order, and the discrete energy lies below the exact one (Galerkin)."""
+    n20, e20 = _steady_errors("20k")
+    n80, e80 = _steady_errors("80k")
+    assert n20 < 5e-4 and n80 < 1.2e-4
+    assert 3.2 < n20 / n80 < 4.8
+    assert e20 < 0 and e80 < 0
+    assert 3.2 < e20 / e80 < 4.8 and abs(e80) < 2e-4
+
+
+def _slowest_mode_error(kind):
+    """Slowest mode exp(-lam t) R(r): R = J0(k r) Y0(k R_IN) - Y0(k r) J0(k R_IN)
+    with R(R_OUT) = 0, lam = nu k^2 / sigma."""
+    import scipy.sparse.linalg as spla
+    from scipy.optimize import brentq
+    from scipy.special import j0, y0
+    f = lambda k: j0(k * R_IN) * y0(k * R_OUT) - y0(k * R_IN) * j0(k * R_OUT)
+    ks = np.linspace(1.0, 200.0, 4000)
+    v = f(ks)
+    i = np.flatnonzero(np.sign(v[:-1]) != np.sign(v[1:]))[0]
+    k1 = brentq(f, ks[i], ks[i + 1], xtol=1e-14)
+    lam = NU_ANN * k1 ** 2 / SIGMA_ANN
+    _, d = _uniform_annulus(kind, SIGMA_ANN, 0.0, False)
+    lam_h = spla.eigsh(d.K.tocsc(), k=1, M=d.M.tocsc(), sigma=0.0, which="LM",
+                       return_eigenvectors=False)[0]
+    return (lam_h - lam) / lam
+
+
+def test_annulus_slowest_mode_matches_the_bessel_root():
+    """M and K (Eq. 4) together on the annulus: the smallest generalised
+    eigenvalue of (K, M) approaches the slowest radial mode's decay rate from
+    above (Rayleigh-Ritz with the consistent mass) at second order."""
+    d20 = _slowest_mode_error("20k")
+    d80 = _slowest_mode_error("80k")
+    assert d20 > 0 and d80 > 0
+    assert d80 < 1.5e-4
+    assert 3.2 < d20 / d80 < 4.8
